@@ -1,0 +1,206 @@
+/*
+ * rp.h -- C ABI of the GB300 library for the stochastic spin-coherent-state
+ * trace of radical-pair recombination yields (Lewis, Fay and Manolopoulos,
+ * "An efficient quantum mechanical method for radical pair recombination
+ * reactions").
+ *
+ * Model (Sec. II):
+ *   H   = omega (S_1z + S_2z) + 2 J S_1.S_2 + sum_k S_{i(k)} . A_k . I_k     (Eq. 1)
+ *         omega = |gamma_e| B with B along z; the paper's isotropic coupling
+ *         a_ik I.S is the special case A_k = a_k 1.
+ *   K   = k_S/2 P_S + k_T/2 P_T                                               (Eq. 2)
+ *   P_S = 1/4 - S_1.S_2,   P_T = 3/4 + S_1.S_2                                (Eqs. 3-4)
+ *   |S, Omega; t> = exp(-iHt - Kt) |S> x prod_k |Omega_k>                   (Eqs. 13, 15, 19)
+ *   phi_S(Omega) = k_S int_0^T <S,Omega;t| P_S |S,Omega;t> dt                 (Eq. 22, truncated at T)
+ *   Phi_S(B) ~ (1/M) sum_s phi_S(Omega_s),  SE = sigma / sqrt(M)              (Eqs. 18, 20, 23)
+ * The triplet yield is Phi_T = 1 - survival(T) - Phi_S, which follows from
+ * d|psi|^2/dt = -k_S <P_S> - k_T <P_T> for the Haberkorn generator (Eq. 2).
+ *
+ * Units: fields, hyperfine tensors and J in mT; rates in us^-1; times in us.
+ * Internally energies are in rad/us (value in mT times |gamma_e|).
+ *
+ * Conventions for every entry point:
+ *   - Host pointers are caller-owned; they are read or written during the
+ *     call only and never retained.  Device pointers (named *_dev) must be
+ *     CUDA device memory on the current device.
+ *   - Every function returns an rp_status; no C++ exception crosses the ABI.
+ *     On failure, rp_last_error() returns a thread-local message.
+ *   - An rp_system is owned by the library from rp_create to rp_destroy.
+ *     Calls on one system are not thread-safe.
+ *   - Compute entry points run on the CUDA stream given in rp_options.stream
+ *     (or the per-thread default stream when NULL) and synchronise that
+ *     stream before returning, so host outputs are complete on return.
+ *
+ * State vector layout (rp_apply_h, rp_init_states): complex interleaved
+ * (re, im) in double (RP_FP64) or float (RP_FP32).  Element (m, e) of vector
+ * v is at complex index v * 4Z + 4 m + e, where e = 2 e_1 + e_2 with
+ * e_i = 0 for alpha (m_s = +1/2) and 1 for beta, and m = sum_p j_p stride_p
+ * is the nuclear configuration in the library's nucleus order (see
+ * rp_layout): position p = 0 is the innermost nucleus, stride_0 = 1,
+ * stride_{p+1} = stride_p (2 I_p + 1), and digit j_p = I_p - M_p counts down
+ * from M_p = +I_p.
+ */
+#ifndef RP_H_
+#define RP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rp_system rp_system; /* opaque, library-owned */
+
+typedef enum rp_status {
+  RP_OK = 0,
+  RP_EINVAL = 1,    /* invalid argument (message in rp_last_error) */
+  RP_ENOMEM = 2,    /* device or host allocation failed */
+  RP_ECUDA = 3,     /* a CUDA runtime call or kernel launch failed */
+  RP_ETIMEOUT = 4,  /* a bounded device wait gave up */
+  RP_ENOTCONV = 5,  /* the propagation plan could not reach the tolerance */
+  RP_ENOTIMPL = 6,  /* option combination not implemented */
+  RP_ENODEV = 7     /* no usable CUDA device (sm_103a) */
+} rp_status;
+
+enum { RP_FP64 = 0, RP_FP32 = 1 };
+
+/* Options of the compute entry points.  rp_default_options fills defaults. */
+typedef struct rp_options {
+  int precision;          /* RP_FP64 or RP_FP32: storage and arithmetic of the
+                             state vectors; time integrals, Chebyshev
+                             coefficients and averages are FP64 always */
+  int n_cheb;             /* Chebyshev terms per macro-step, multiple of 4 in [8, 96]
+                             (0: 64 FP64, 40 FP32) */
+  double tol;             /* truncation bound per macro-step (0: 1e-15 FP64, 1e-9 FP32) */
+  int max_rows;           /* concurrent propagations (0: from free device memory) */
+  int deterministic;      /* 1: trace over the Z basis states |S, M> (Eq. 14)
+                             instead of M coherent-state samples; M is ignored */
+  long long sample_offset;/* first sample index (resume / sharding) */
+  uint32_t pair_id;       /* Philox counter word 3 (radical-pair id) */
+  int profile;            /* 1: time the H.psi step kernels with CUDA events */
+  void* stream;           /* cudaStream_t, NULL: per-thread default stream */
+} rp_options;
+
+/* Per-call statistics (optional output of rp_yields). */
+typedef struct rp_stats {
+  long long kernel_launches;    /* kernels launched by the call */
+  long long step_launches;      /* of which H.psi Chebyshev step kernels */
+  long long row_terms;          /* sum over propagations of Chebyshev terms */
+  long long propagations;       /* (field, sample) propagations run */
+  double step_bytes;            /* algorithmic bytes of the timed step launches */
+  double step_ms;               /* CUDA-event time of the timed step launches (profile=1) */
+  long long step_launches_timed;/* step launches inside the timed intervals */
+  double device_ms;             /* CUDA-event time of the whole call on its stream */
+  int rows;                     /* concurrent propagations used */
+  int n_cheb;                   /* Chebyshev terms per macro-step used */
+  long long h2d_bytes;          /* host-to-device bytes copied by the call */
+  long long d2h_bytes;          /* device-to-host bytes copied by the call */
+} rp_stats;
+
+/* Propagation plan of one field (rp_plan_field; host logic, no GPU needed). */
+typedef struct rp_field_plan {
+  double E_min, E_max;   /* rigorous bounds on the spectrum of H (rad/us) */
+  double E_c, dE;        /* Chebyshev centre and half-width (rad/us) */
+  double h;              /* macro-step length (us) */
+  long long n_macro;     /* macro-steps to reach t_max */
+  int n_cheb;            /* terms per macro-step */
+  double tail;           /* truncation bound of the plan */
+  double kbar;           /* (k_S + k_T)/2, factored out of the propagator */
+  double kappa;          /* (k_S - k_T)/4, remaining non-Hermitian part */
+} rp_field_plan;
+
+/* Device allocator hooks: alloc(bytes, stream, ctx) -> device pointer or
+ * NULL; free(ptr, stream, ctx).  NULL restores cudaMallocAsync/cudaFreeAsync. */
+typedef void* (*rp_alloc_fn)(size_t bytes, void* stream, void* ctx);
+typedef void (*rp_free_fn)(void* ptr, void* stream, void* ctx);
+
+/* Library version string. */
+const char* rp_version(void);
+
+/* Human-readable name of a status code (static storage). */
+const char* rp_status_str(rp_status s);
+
+/* Thread-local message of the last failure in this thread ("" if none). */
+const char* rp_last_error(void);
+
+/* Fill *opt with defaults: RP_FP32, n_cheb 0, tol 0, max_rows 0,
+ * deterministic 0, sample_offset 0, pair_id 0, profile 0, stream NULL. */
+void rp_default_options(rp_options* opt);
+
+/* Route the library's device allocations through the caller's allocator
+ * (e.g. a framework's caching allocator).  Process-wide. */
+rp_status rp_set_allocator(rp_alloc_fn alloc, rp_free_fn free_fn, void* ctx);
+
+/* Create a radical-pair system (Eq. 1 with Eqs. 2-4).
+ *   n_nuc     number of nuclei, 0 <= n_nuc <= 24
+ *   radical   [n_nuc] 0 or 1: the electron each nucleus couples to
+ *   two_I     [n_nuc] twice the nuclear spin, 1 <= two_I <= 9
+ *   A         [n_nuc * 9] hyperfine tensors in mT, row-major 3x3, symmetric
+ *             to 1e-12 relative (the isotropic a_k of Eq. 1 is a_k * identity)
+ *   k_S, k_T  recombination rates (us^-1), finite, >= 0, not both 0 (Eq. 2)
+ *   J         exchange coupling in mT, entering as +2J S_1.S_2 (Eq. 1)
+ * Z = prod(2 I_k + 1) must not exceed 2^31.  Host-only: needs no GPU.
+ * Errors: RP_EINVAL on any violated condition, RP_ENOMEM. */
+rp_status rp_create(int n_nuc, const int* radical, const int* two_I, const double* A,
+                    double k_S, double k_T, double J, rp_system** out);
+
+/* Release a system (NULL is ignored). */
+void rp_destroy(rp_system* sys);
+
+/* Nucleus order of the state layout: order[p] = input index of the nucleus at
+ * position p (p = 0 innermost); *Z_out = number of nuclear states.  Either
+ * output may be NULL. */
+rp_status rp_layout(const rp_system* sys, int* order, long long* Z_out);
+
+/* Host planner for field B (mT) and horizon t_max (us): spectral bounds of H
+ * by Weyl's inequality over the electron block and each hyperfine block, the
+ * Chebyshev centre and half-width, and the macro-step h chosen so that the
+ * truncated series stays below tol.  Optionally returns the n_cheb
+ * propagation coefficients c_n (complex, 2 doubles each; they include the
+ * factored decay exp(-kbar h / 2)) and the n_cheb x n_cheb time-integral
+ * weights W_nm (complex, row-major) of one macro-step.  Host-only.
+ * precision/n_cheb/tol as in rp_options (0 = defaults).
+ * Errors: RP_EINVAL, RP_ENOTCONV. */
+rp_status rp_plan_field(const rp_system* sys, double B, double t_max, int precision,
+                        int n_cheb, double tol, rp_field_plan* plan,
+                        double* coef, double* W);
+
+/* Singlet and triplet yields over a field sweep (Eqs. 18, 20, 22, 23).
+ *   fields      [n_fields] field strengths B in mT (n_fields >= 0; 0 is a no-op)
+ *   M           coherent-state samples per field, >= 2 (ignored when
+ *               opt->deterministic, which uses the Z basis states |S, M>)
+ *   seed        Philox key; sample s of nucleus k draws counter
+ *               (k, s_lo, s_hi, pair_id) with key (seed_lo, seed_hi)
+ *   t_max       horizon T > 0 (us)
+ *   opt         NULL for defaults
+ *   out         [n_fields * 5] host: Phi_S, Phi_T, SE_S, SE_T, mean survival
+ *   per_sample  [n_fields * M * 3] host or NULL: phi_S, phi_T, survival of
+ *               each (field, sample), field-major (M = Z when deterministic)
+ *   stats       optional host output
+ * Every sample uses the same directions at every field (common random numbers).
+ * Errors: RP_EINVAL, RP_ENOMEM, RP_ECUDA, RP_ENOTCONV, RP_ENODEV. */
+rp_status rp_yields(rp_system* sys, int n_fields, const double* fields, int M, uint64_t seed,
+                    double t_max, const rp_options* opt, double* out, double* per_sample,
+                    rp_stats* stats);
+
+/* y = (H - iK) x for n_vec state vectors in the layout above, field B (mT);
+ * x_dev and y_dev are device arrays of n_vec * 4Z complex values in the
+ * precision given, and must not overlap.  Stream as in rp_options (may be
+ * NULL).  Errors: RP_EINVAL, RP_ECUDA. */
+rp_status rp_apply_h(rp_system* sys, double B, int precision, int n_vec, const void* x_dev,
+                     void* y_dev, void* stream);
+
+/* Initial states |S> x prod_k |Omega_k> (Eqs. 15, 19) of samples
+ * sample0 .. sample0 + n - 1 written to psi_dev (n * 4Z complex, precision as
+ * given).  angles, if not NULL, receives [n * n_nuc * 2] host doubles: the
+ * uniforms (u1, u2) of each nucleus in input order, with cos(theta) = 1 - 2 u1
+ * and phi = 2 pi u2.  Errors: RP_EINVAL, RP_ECUDA, RP_ENODEV. */
+rp_status rp_init_states(rp_system* sys, int precision, uint64_t seed, uint32_t pair_id,
+                         long long sample0, int n, void* psi_dev, double* angles, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RP_H_ */

@@ -1,0 +1,95 @@
+// Device-side data structures and kernel launchers of the radical-pair
+// propagation (stochastic trace, Eqs. 13-23 of Lewis, Fay and Manolopoulos).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rp {
+
+constexpr int kMaxNucDev = 24;
+
+// Field-independent Hamiltonian constants in the layout order (rad/us).
+// Per nucleus at position p: electron rad[p] (0 or 1), dimension d[p],
+// configuration stride stride[p], the 2x2 electron matrix
+//   U_p = sum_a u_a S_a,  u_a = (A_ax - i A_ay)/2,
+// that multiplies I_+ in S.A.I = sum_a S_a (u_a I_+ + conj(u_a) I_- + A_az I_z),
+// stored row-major as (re, im) pairs, and the column (A_xz, A_yz, A_zz).
+template <typename T>
+struct HamDev {
+  long long Z;
+  int n_nuc, n_half, n_one, aniso;
+  T Je;     // 2J S1.S2 coupling J in rad/us
+  T kappa;  // (k_S - k_T)/4: H' = H - i kappa (P_S - P_T)
+  int rad[kMaxNucDev];
+  int d[kMaxNucDev];
+  long long stride[kMaxNucDev];
+  T U[kMaxNucDev][8];
+  T v[kMaxNucDev][3];
+};
+
+// Per-field scalars: Zeeman omega, 1/dE and the shift sh with
+// z = (1/dE) H' a - sh a  (sh = E_c/dE for propagation).
+template <typename T>
+struct FieldDev {
+  T omega, s, sh_re, sh_im;
+};
+
+enum StepMode { MODE_APPLY = 0, MODE_FIRST = 1, MODE_MID = 2, MODE_LAST = 3 };
+
+// Per-row (one propagation) metadata, device arrays of length rows.
+struct RowsDev {
+  int* field;        // field index
+  int* n_macro;      // macro-steps this row needs
+  long long* sample; // sample index (coherent) or basis index (deterministic)
+  long long* out;    // output slot field * M + sample_rel
+  double* integral;  // int |P_S psi|^2 dt accumulated (FP64)
+  double* survival;  // |psi(T)|^2
+};
+
+// Layout description for the state-initialisation kernels.
+struct LayoutDev {
+  long long Z;
+  int n_nuc, n_half, n_one;
+  int d[kMaxNucDev];
+  int input_index[kMaxNucDev];  // Philox counter word 0 of the nucleus at position p
+  long long stride[kMaxNucDev];
+};
+
+// ---- launchers (return cudaGetLastError after the launch) ----
+
+cudaError_t launch_coherent_amps(const LayoutDev& L, const long long* row_sample, int rows,
+                                 uint64_t seed, uint32_t pair, double* amps, double* uv,
+                                 cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_init_state(const LayoutDev& L, const double* amps, const long long* row_sample,
+                              int rows, int deterministic, T* psi, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_step(const HamDev<T>& H, const FieldDev<T>* fields, const int* row_field,
+                        const int* row_nmacro, long long macro, int rows, const T* cur,
+                        const T* prev, T* next, T* acc, T* X, const T* coef, int n_c, int n,
+                        int mode, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_gram(const T* X, double* G, const int* row_nmacro, long long macro, int rows,
+                        long long Z, int n_c, cudaStream_t st);
+
+cudaError_t launch_integrate(double* G, const double* W, const int* row_field,
+                             const int* row_nmacro, long long macro, int rows, int n_c,
+                             double* integral, cudaStream_t st);
+
+template <typename T>
+cudaError_t launch_norm(const T* S0, const T* S1, const int* row_nmacro, int rows, long long Z,
+                        double* survival, cudaStream_t st);
+
+cudaError_t launch_finalize(const RowsDev& R, int rows, double k_S, double* per_sample,
+                            cudaStream_t st);
+
+cudaError_t launch_stats(const double* per_sample, int n_fields, long long M, double* out,
+                         cudaStream_t st);
+
+cudaError_t launch_zero(double* p, size_t n, cudaStream_t st);
+
+}  // namespace rp

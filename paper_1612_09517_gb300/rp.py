@@ -1,0 +1,272 @@
+"""Thin Python binding of the C ABI in ``include/rp.h`` (argument marshalling only).
+
+Every computation runs inside ``_lib/librp.so`` (sm_103a CUDA kernels and the
+host planner).  Importing this module loads the library and fails loudly if it
+has not been built: there is no CPU fallback.
+
+The functions carry the C names: ``rp_create``, ``rp_destroy``, ``rp_layout``,
+``rp_plan_field``, ``rp_yields``, ``rp_apply_h``, ``rp_init_states`` ... and
+``System`` wraps an ``rp_system*`` for convenience.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "librp.so")
+
+RP_FP64 = 0
+RP_FP32 = 1
+STATUS = ["RP_OK", "RP_EINVAL", "RP_ENOMEM", "RP_ECUDA", "RP_ETIMEOUT", "RP_ENOTCONV",
+          "RP_ENOTIMPL", "RP_ENODEV"]
+
+
+class RPError(RuntimeError):
+    def __init__(self, status, msg):
+        self.status = status
+        name = STATUS[status] if 0 <= status < len(STATUS) else str(status)
+        super().__init__(f"{name}: {msg}")
+
+
+class rp_options(C.Structure):
+    _fields_ = [("precision", C.c_int), ("n_cheb", C.c_int), ("tol", C.c_double),
+                ("max_rows", C.c_int), ("deterministic", C.c_int),
+                ("sample_offset", C.c_longlong), ("pair_id", C.c_uint32),
+                ("profile", C.c_int), ("stream", C.c_void_p)]
+
+
+class rp_stats(C.Structure):
+    _fields_ = [("kernel_launches", C.c_longlong), ("step_launches", C.c_longlong),
+                ("row_terms", C.c_longlong), ("propagations", C.c_longlong),
+                ("step_bytes", C.c_double), ("step_ms", C.c_double),
+                ("step_launches_timed", C.c_longlong), ("device_ms", C.c_double),
+                ("rows", C.c_int), ("n_cheb", C.c_int), ("h2d_bytes", C.c_longlong),
+                ("d2h_bytes", C.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class rp_field_plan(C.Structure):
+    _fields_ = [("E_min", C.c_double), ("E_max", C.c_double), ("E_c", C.c_double),
+                ("dE", C.c_double), ("h", C.c_double), ("n_macro", C.c_longlong),
+                ("n_cheb", C.c_int), ("tail", C.c_double), ("kbar", C.c_double),
+                ("kappa", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+# (name, restype, argtypes) of every exported symbol declared in include/rp.h
+SIGNATURES = [
+    ("rp_version", C.c_char_p, []),
+    ("rp_status_str", C.c_char_p, [C.c_int]),
+    ("rp_last_error", C.c_char_p, []),
+    ("rp_default_options", None, [C.POINTER(rp_options)]),
+    ("rp_set_allocator", C.c_int, [ALLOC_FN, FREE_FN, C.c_void_p]),
+    ("rp_create", C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                            C.POINTER(C.c_double), C.c_double, C.c_double, C.c_double,
+                            C.POINTER(C.c_void_p)]),
+    ("rp_destroy", None, [C.c_void_p]),
+    ("rp_layout", C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_longlong)]),
+    ("rp_plan_field", C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_int, C.c_int, C.c_double,
+                                C.POINTER(rp_field_plan), C.POINTER(C.c_double),
+                                C.POINTER(C.c_double)]),
+    ("rp_yields", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_int, C.c_uint64,
+                            C.c_double, C.POINTER(rp_options), C.POINTER(C.c_double),
+                            C.POINTER(C.c_double), C.POINTER(rp_stats)]),
+    ("rp_apply_h", C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                             C.c_void_p]),
+    ("rp_init_states", C.c_int, [C.c_void_p, C.c_int, C.c_uint64, C.c_uint32, C.c_longlong,
+                                 C.c_int, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
+]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run __graft_entry__.build() (or "
+                          f"python paper_1612_09517_gb300/build.py) first; there is no CPU fallback")
+    lib = C.CDLL(LIB_PATH)
+    for name, res, args in SIGNATURES:
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+LIB = _load()
+
+
+def _check(st):
+    if st != 0:
+        raise RPError(st, LIB.rp_last_error().decode())
+
+
+def _dptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def rp_version() -> str:
+    return LIB.rp_version().decode()
+
+
+def rp_default_options(**kw) -> rp_options:
+    o = rp_options()
+    LIB.rp_default_options(C.byref(o))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = {"fp64": RP_FP64, "fp32": RP_FP32}[v.lower()]
+        setattr(o, k, v)
+    return o
+
+
+def rp_create(radical, two_I, A, k_S, k_T, J):
+    radical = np.ascontiguousarray(radical, dtype=np.int32).reshape(-1)
+    two_I = np.ascontiguousarray(two_I, dtype=np.int32).reshape(-1)
+    A = np.ascontiguousarray(A, dtype=np.float64).reshape(-1)
+    n = radical.size
+    h = C.c_void_p()
+    _check(LIB.rp_create(n, radical.ctypes.data_as(C.POINTER(C.c_int)),
+                         two_I.ctypes.data_as(C.POINTER(C.c_int)), _dptr(A), float(k_S),
+                         float(k_T), float(J), C.byref(h)))
+    return h
+
+
+def rp_destroy(h):
+    LIB.rp_destroy(h)
+
+
+def rp_layout(h, n_nuc):
+    order = np.zeros(max(n_nuc, 1), dtype=np.int32)
+    Z = C.c_longlong()
+    _check(LIB.rp_layout(h, order.ctypes.data_as(C.POINTER(C.c_int)), C.byref(Z)))
+    return order[:n_nuc], int(Z.value)
+
+
+def rp_plan_field(h, B, t_max, precision=RP_FP64, n_cheb=0, tol=0.0, with_coef=False):
+    p = rp_field_plan()
+    n_c = n_cheb or (64 if precision == RP_FP64 else 40)
+    coef = np.zeros(2 * n_c) if with_coef else None
+    W = np.zeros(2 * n_c * n_c) if with_coef else None
+    _check(LIB.rp_plan_field(h, float(B), float(t_max), precision, n_cheb, float(tol), C.byref(p),
+                             _dptr(coef) if with_coef else None, _dptr(W) if with_coef else None))
+    d = p.as_dict()
+    if with_coef:
+        d["coef"] = coef.view(np.complex128)
+        d["W"] = W.view(np.complex128).reshape(n_c, n_c)
+    return d
+
+
+def rp_yields(h, fields, M, seed, t_max, opt=None, per_sample=False, Z=None):
+    fields = np.ascontiguousarray(fields, dtype=np.float64).reshape(-1)
+    nf = fields.size
+    o = opt if opt is not None else rp_default_options()
+    out = np.zeros(max(nf * 5, 1))
+    Mr = Z if o.deterministic else M
+    ps = np.zeros(max(nf * Mr * 3, 1)) if per_sample else None
+    stats = rp_stats()
+    _check(LIB.rp_yields(h, nf, _dptr(fields), int(M), C.c_uint64(int(seed)), float(t_max),
+                         C.byref(o), _dptr(out), _dptr(ps) if per_sample else None,
+                         C.byref(stats)))
+    res = {"out": out[: nf * 5].reshape(nf, 5), "stats": stats.as_dict()}
+    if per_sample:
+        res["per_sample"] = ps[: nf * Mr * 3].reshape(nf, Mr, 3)
+    return res
+
+
+def rp_apply_h(h, B, precision, n_vec, x_ptr, y_ptr, stream=None):
+    _check(LIB.rp_apply_h(h, float(B), precision, int(n_vec), C.c_void_p(x_ptr),
+                          C.c_void_p(y_ptr), C.c_void_p(stream or 0)))
+
+
+def rp_init_states(h, precision, seed, pair_id, sample0, n, psi_ptr, n_nuc, stream=None):
+    uv = np.zeros(max(n * n_nuc * 2, 1))
+    _check(LIB.rp_init_states(h, precision, C.c_uint64(int(seed)), C.c_uint32(pair_id),
+                              int(sample0), int(n), C.c_void_p(psi_ptr), _dptr(uv),
+                              C.c_void_p(stream or 0)))
+    return uv[: n * n_nuc * 2].reshape(n, n_nuc, 2)
+
+
+_ALLOC_KEEP = []
+
+
+def use_torch_allocator():
+    """Route library device allocations through PyTorch's caching allocator."""
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device(),
+                                                      stream or 0)
+        except Exception:
+            return None
+
+    def _free(ptr, stream, ctx):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    a, f = ALLOC_FN(_alloc), FREE_FN(_free)
+    _ALLOC_KEEP[:] = [a, f]
+    _check(LIB.rp_set_allocator(a, f, None))
+
+
+class System:
+    """An ``rp_system`` created from a spin system (radical, two_I, A, k_S, k_T, J)."""
+
+    def __init__(self, spin_system):
+        s = spin_system
+        self.spin_system = s
+        self.n_nuc = int(np.asarray(s.radical).size)
+        self.handle = rp_create(s.radical, s.two_I, s.A, s.k_S, s.k_T, s.J)
+        self.order, self.Z = rp_layout(self.handle, self.n_nuc)
+
+    def close(self):
+        if self.handle:
+            rp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def plan(self, B, t_max, **kw):
+        return rp_plan_field(self.handle, B, t_max, **kw)
+
+    def yields(self, fields, M, seed, t_max, per_sample=False, **opt):
+        o = rp_default_options(**opt)
+        return rp_yields(self.handle, fields, M, seed, t_max, o, per_sample, Z=self.Z)
+
+    def to_input_order(self, psi):
+        """Permute library-layout state vectors (..., 4Z) to the oracle's kron order
+        (electron 1, electron 2, nuclei in input order)."""
+        psi = np.asarray(psi)
+        lead = psi.shape[:-1]
+        dims_pos = [int(self.spin_system.two_I[k]) + 1 for k in self.order]
+        # library index: ((j_{N-1} ... j_0) , e1, e2) with position 0 innermost
+        t = psi.reshape(*lead, *dims_pos[::-1], 2, 2)
+        nl = len(lead)
+        npos = len(dims_pos)
+        # axes of t after lead: positions N-1..0, then e1, e2
+        pos_axis = {p: nl + (npos - 1 - p) for p in range(npos)}
+        inv = {int(k): p for p, k in enumerate(self.order)}
+        perm = list(range(nl)) + [nl + npos, nl + npos + 1] + [pos_axis[inv[k]] for k in range(npos)]
+        return np.transpose(t, perm).reshape(*lead, -1)
+
+    def from_input_order(self, psi):
+        psi = np.asarray(psi)
+        lead = psi.shape[:-1]
+        nl = len(lead)
+        npos = self.n_nuc
+        dims_in = [int(d) + 1 for d in self.spin_system.two_I]
+        t = psi.reshape(*lead, 2, 2, *dims_in)
+        inv = {int(k): p for p, k in enumerate(self.order)}
+        # target axes: positions N-1..0 (input index order[p]), then e1, e2
+        perm = list(range(nl)) + [nl + 2 + int(self.order[p]) for p in range(npos - 1, -1, -1)] + [nl, nl + 1]
+        return np.transpose(t, perm).reshape(*lead, -1)

@@ -1,0 +1,235 @@
+"""GPU parity: the sm_103a path through the C ABI against the FP64 CPU oracle.
+
+Tolerances (per-sample yields phi_S, phi_T of Eq. 22 truncated at T):
+* FP64 path: 1e-10 relative.  The plan bounds the Chebyshev truncation by
+  1e-15 per macro-step; FP64 rounding over ~1e2-1e4 macro-steps stays far below.
+* FP32 path: 1e-5 relative.  FP32 storage rounds each term at 6e-8; the
+  accumulated random walk over the macro-steps of these horizons stays below.
+Survival |psi(T)|^2 is compared in absolute terms at the same levels.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import chebyshev, coherent, dense, philox, spin
+from paper_1612_09517_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    torch.cuda.set_device(0)
+    from paper_1612_09517_gb300 import rp
+    rp.use_torch_allocator()
+    yield
+
+
+def _rp():
+    from paper_1612_09517_gb300 import rp
+    return rp
+
+
+TOL = {"fp64": 1e-10, "fp32": 1e-5}
+
+
+def _cmp_per_sample(got, phS, phT, surv, prec):
+    tol = TOL[prec]
+    eS = np.max(np.abs(got[:, 0] - phS) / np.maximum(np.abs(phS), 1e-3))
+    # phi_T = 1 - survival - phi_S is derived by conservation, so its error is
+    # measured on the scale of the yields (max(|phi_T|, |phi_S|))
+    eT = np.max(np.abs(got[:, 1] - phT) / np.maximum(np.maximum(np.abs(phT), np.abs(phS)), 1e-3))
+    eU = np.max(np.abs(got[:, 2] - surv))
+    assert eS < tol and eT < tol and eU < tol, (eS, eT, eU)
+    return max(eS, eT)
+
+
+MIXED = [
+    ("config1", lambda: wl.config1().system),
+    ("aniso_mixed", lambda: wl.random_anisotropic(2, 1, two_I=[1, 2, 1], k_S=2.0, k_T=0.5, J=0.3, seed=40)),
+    ("spin3half_J", lambda: wl.random_isotropic(1, 2, two_I=[3, 1, 2], k_S=0.2, k_T=5.0, J=-0.5, seed=41)),
+    ("no_nuclei", lambda: wl.SpinSystem([], [], np.zeros((0, 3, 3)), 1.5, 0.7, 0.4)),
+    ("ragged_z", lambda: wl.random_isotropic(3, 2, two_I=[2, 1, 2, 2, 1], k_S=1.0, k_T=2.0, seed=42)),
+]
+
+
+# ------------------------------------------------------------ initial states
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name,mk", MIXED, ids=[m[0] for m in MIXED])
+def test_initial_states_match_oracle(name, mk, prec):
+    rp = _rp()
+    s = mk()
+    sy = rp.System(s)
+    n, sample0, seed, pair = 5, 3, 12345678901, 7
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    psi = torch.zeros(n * 4 * sy.Z * 2, dtype=dt, device="cuda")
+    uv = rp.rp_init_states(sy.handle, rp.RP_FP64 if prec == "fp64" else rp.RP_FP32, seed, pair,
+                           sample0, n, psi.data_ptr(), sy.n_nuc)
+    if sy.n_nuc:
+        u1, u2 = philox.draw_uniforms(seed, pair, np.arange(sample0, sample0 + n), sy.n_nuc)
+        # integer work: the 53-bit uniforms must agree bit for bit
+        assert np.array_equal(uv[..., 0], u1) and np.array_equal(uv[..., 1], u2)
+    got = psi.cpu().numpy().view(np.complex128 if prec == "fp64" else np.complex64)
+    got = sy.to_input_order(got.reshape(n, 4 * sy.Z))
+    ref = coherent.sample_states(s, seed, np.arange(sample0, sample0 + n), pair=pair)
+    assert np.max(np.abs(got - ref)) < (1e-14 if prec == "fp64" else 2e-7)
+
+
+# --------------------------------------------------------------------- H psi
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name,mk", MIXED, ids=[m[0] for m in MIXED])
+def test_apply_h_matches_dense(name, mk, prec):
+    """(H - iK) x of the kernel against the oracle's dense Eq. 1 - Eq. 2 matrix."""
+    rp = _rp()
+    s = mk()
+    sy = rp.System(s)
+    rng = np.random.default_rng(5)
+    n_vec = 3
+    x = rng.normal(size=(n_vec, 4 * sy.Z)) + 1j * rng.normal(size=(n_vec, 4 * sy.Z))
+    for B in (0.0, 2.3, -7.1):
+        Heff = spin.hamiltonian(s, B) - 1j * spin.haberkorn(s)
+        ref = x @ Heff.T
+        cdt = np.complex128 if prec == "fp64" else np.complex64
+        xl = np.ascontiguousarray(sy.from_input_order(x).astype(cdt))
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        xd = torch.from_numpy(xl.view(np.float64 if prec == "fp64" else np.float32).copy()).to("cuda")
+        yd = torch.zeros_like(xd)
+        rp.rp_apply_h(sy.handle, B, rp.RP_FP64 if prec == "fp64" else rp.RP_FP32, n_vec,
+                      xd.data_ptr(), yd.data_ptr())
+        got = sy.to_input_order(yd.cpu().numpy().view(cdt).reshape(n_vec, -1))
+        err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+        assert err < (1e-13 if prec == "fp64" else 2e-6), err
+
+
+# ----------------------------------------------------------- yields, config 1
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_config1_per_sample_parity(prec):
+    """Config 1 in full (11 fields in 0-5 mT, M = 64, seed 0, T = 10 us)."""
+    rp = _rp()
+    w = wl.config1()
+    s = w.system
+    sy = rp.System(s)
+    res = sy.yields(w.fields, w.M, w.seed, w.t_max, per_sample=True, precision=prec)
+    psi0 = coherent.sample_states(s, w.seed, range(w.M))
+    worst = 0.0
+    for i, B in enumerate(w.fields):
+        phS, phT, surv = dense.sample_yields(s, B, w.t_max, psi0)
+        worst = max(worst, _cmp_per_sample(res["per_sample"][i], phS, phT, surv, prec))
+        # per-field mean and standard error (Eq. 18, Eq. 23) of the device reduction
+        mS, seS = dense.estimate(res["per_sample"][i][:, 0])
+        assert abs(res["out"][i, 0] - mS) < 1e-14 and abs(res["out"][i, 2] - seS) < 1e-14
+        mO, _ = dense.estimate(phS)
+        assert abs(res["out"][i, 0] - mO) < TOL[prec]
+    print(f"config1 {prec}: worst relative per-sample error {worst:.2e}")
+
+
+def test_side_case_closed_form():
+    """One spin-1/2, a = 1 mT, k = 1 us^-1, T = 10 us: Phi_S = 0.6249838157 (closed form)."""
+    rp = _rp()
+    sy = rp.System(wl.one_nucleus(1.0, 1, 1.0))
+    for prec, tol in (("fp64", 1e-10), ("fp32", 1e-5)):
+        r = sy.yields([0.0], 2, 0, 10.0, precision=prec, deterministic=1)
+        assert abs(r["out"][0, 0] - 0.6249838157) < tol
+        r = sy.yields([0.0], 8, 3, 10.0, per_sample=True, precision=prec)
+        assert np.max(np.abs(r["per_sample"][0, :, 0] - 0.6249838157)) < tol
+
+
+def test_deterministic_trace_matches_oracle():
+    """Eq. 14 on the GPU (Z basis states) against tr[Y P_S]/Z of the oracle."""
+    rp = _rp()
+    s = wl.random_anisotropic(2, 1, two_I=[1, 2, 1], k_S=2.0, k_T=0.5, J=0.3, seed=40)
+    sy = rp.System(s)
+    fields = np.array([0.0, 1.5, -1.5])
+    r = sy.yields(fields, 2, 0, 3.0, precision="fp64", deterministic=1)
+    for i, B in enumerate(fields):
+        ref = dense.trace_yields(s, B, 3.0)
+        assert abs(r["out"][i, 0] - ref[0]) < 1e-10 * abs(ref[0])
+        assert abs(r["out"][i, 1] - ref[1]) < 1e-10 * abs(ref[1])
+        assert abs(r["out"][i, 4] - ref[2]) < 1e-12
+    # field-reversal symmetry of the trace
+    assert abs(r["out"][1, 0] - r["out"][2, 0]) < 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name,mk", MIXED[1:], ids=[m[0] for m in MIXED[1:]])
+def test_mixed_systems_per_sample(name, mk, prec):
+    """Anisotropic tensors, spin 1 and 3/2, J != 0, k_S != k_T, no nuclei, ragged Z."""
+    rp = _rp()
+    s = mk()
+    sy = rp.System(s)
+    fields = np.array([0.0, 0.8, 3.0])
+    T, M = 2.5, 6
+    r = sy.yields(fields, M, 11, T, per_sample=True, precision=prec)
+    psi0 = coherent.sample_states(s, 11, range(M))
+    for i, B in enumerate(fields):
+        phS, phT, surv = dense.sample_yields(s, B, T, psi0)
+        _cmp_per_sample(r["per_sample"][i], phS, phT, surv, prec)
+
+
+def test_no_nuclei_closed_form():
+    rp = _rp()
+    sy = rp.System(wl.SpinSystem([], [], np.zeros((0, 3, 3)), 1.5, 0.7, 0.4))
+    r = sy.yields([0.0, 4.0], 2, 0, 1.3, precision="fp64")
+    assert np.allclose(r["out"][:, 0], 1 - math.exp(-1.5 * 1.3), atol=1e-12)
+    assert np.allclose(r["out"][:, 1], 0.0, atol=1e-12)
+
+
+# ------------------------------------------------------- execution invariance
+
+def test_batching_and_offset_invariance():
+    """Row batching (max_rows) and sample_offset do not change any sample's result."""
+    rp = _rp()
+    s = wl.random_isotropic(2, 2, two_I=[1, 2, 1, 1], k_S=1.0, k_T=3.0, J=0.2, seed=7)
+    sy = rp.System(s)
+    fields = [0.0, 1.0, 4.0]
+    a = sy.yields(fields, 8, 5, 2.0, per_sample=True, precision="fp64")
+    b = sy.yields(fields, 8, 5, 2.0, per_sample=True, precision="fp64", max_rows=5)
+    assert np.allclose(a["per_sample"], b["per_sample"], rtol=1e-13, atol=1e-15)
+    c = sy.yields(fields, 4, 5, 2.0, per_sample=True, precision="fp64", sample_offset=4)
+    assert np.allclose(a["per_sample"][:, 4:], c["per_sample"], rtol=1e-13, atol=1e-15)
+
+
+def test_edge_cases():
+    rp = _rp()
+    sy = rp.System(wl.config1().system)
+    # horizon shorter than one macro-step, minimal M
+    r = sy.yields([0.0, 5.0], 2, 0, 1e-4, per_sample=True, precision="fp64")
+    psi0 = coherent.sample_states(wl.config1().system, 0, range(2))
+    for i, B in enumerate([0.0, 5.0]):
+        phS, phT, surv = dense.sample_yields(wl.config1().system, B, 1e-4, psi0)
+        assert np.allclose(r["per_sample"][i, :, 0], phS, rtol=1e-10, atol=1e-16)
+    # k_S = 0: no singlet yield at all
+    s0 = wl.random_isotropic(2, 0, k_S=0.0, k_T=1.0, seed=3)
+    r = rp.System(s0).yields([1.0], 3, 0, 2.0, per_sample=True, precision="fp64")
+    assert np.all(r["per_sample"][0, :, 0] == 0.0)
+    assert r["stats"]["kernel_launches"] > 0
+
+
+# -------------------------------------------- config 2 at full size, sampled
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_config2_full_size_sampled(prec):
+    """Config 2 (Z = 20736, 12 nuclei, k_S != k_T) in the bench's launch form:
+    all rows of a field sweep run together; sampled rows against the oracle's
+    matrix-free FP64 propagation (horizon shortened so the CPU finishes)."""
+    rp = _rp()
+    w = wl.config2()
+    sy = rp.System(w.system)
+    fields = np.array([0.0, 10.0, 3.0, 30.0])
+    M, T = 4, 0.15
+    r = sy.yields(fields, M, 0, T, per_sample=True, precision=prec)
+    psi0 = coherent.sample_states(w.system, 0, [0, 3])
+    for fi, si in ((0, 0), (1, 3)):
+        ref = chebyshev.propagate_yields(w.system, fields[fi], T, psi0[0 if si == 0 else 1])
+        got = r["per_sample"][fi, si]
+        assert abs(got[0] - ref[0]) < TOL[prec] * abs(ref[0])
+        assert abs(got[1] - ref[1]) < TOL[prec] * max(abs(ref[1]), 1e-3)
+        assert abs(got[2] - ref[2]) < TOL[prec]
