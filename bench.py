@@ -183,7 +183,10 @@ def _oracle_curve_terms(t_max, fields):
 
 
 def cpu_oracle_throughput(cores, T_sample, B_list):
-    """Row-terms per second of the FP64 oracle over `cores` spawned processes."""
+    """Row-terms per second of the FP64 oracle over `cores` spawned processes
+    (one BLAS thread each, so the processes do not oversubscribe the cores)."""
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
     ctx = mp.get_context("spawn")
     jobs = [(B_list[i % len(B_list)], T_sample, i) for i in range(cores)]
     t0 = time.perf_counter()
@@ -256,7 +259,7 @@ def run_reference(args):
                            "(M_needed from RP_BENCH_M_NEEDED if set, else per-sample seconds)"},
         "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
                          "sample": f"{cores} processes, each one (field, sample) propagation over "
-                                   f"{T_sample} us at B in {[round(b, 2) for b in B_list]} mT; "
+                                   f"{T_sample} us at B in {[round(float(b), 2) for b in B_list]} mT; "
                                    f"row-terms/s {rate:.0f} extrapolated to {curve_terms} terms per "
                                    "sample over the 64-field curve"},
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -399,7 +402,7 @@ def main():
         cpu = {"value": m_needed * curve_o / rate_cpu, "unit": "s", "cores": cores,
                "kind": "oracle",
                "sample": f"{cores} spawned processes, each one (field, sample) FP64 matrix-free "
-                         f"propagation over {T_sample} us (B in {[round(b, 1) for b in B_list]} mT); "
+                         f"propagation over {T_sample} us (B in {[round(float(b), 1) for b in B_list]} mT); "
                          f"{rate_cpu:.0f} row-terms/s over {wall_cpu:.1f} s, extrapolated to "
                          f"M_needed={m_needed} x {curve_o} oracle terms"}
 

@@ -231,5 +231,6 @@ def test_config2_full_size_sampled(prec):
         ref = chebyshev.propagate_yields(w.system, fields[fi], T, psi0[0 if si == 0 else 1])
         got = r["per_sample"][fi, si]
         assert abs(got[0] - ref[0]) < TOL[prec] * abs(ref[0])
-        assert abs(got[1] - ref[1]) < TOL[prec] * max(abs(ref[1]), 1e-3)
+        # phi_T comes from conservation: error on the scale of the yields
+        assert abs(got[1] - ref[1]) < TOL[prec] * max(abs(ref[1]), abs(ref[0]))
         assert abs(got[2] - ref[2]) < TOL[prec]
