@@ -199,6 +199,27 @@ rp_status rp_apply_h(rp_system* sys, double B, int precision, int n_vec, const v
 rp_status rp_init_states(rp_system* sys, int precision, uint64_t seed, uint32_t pair_id,
                          long long sample0, int n, void* psi_dev, double* angles, void* stream);
 
+/* rp_yields without device allocation.  The paper has no counterpart: this
+ * entry point exists for callers that must not allocate device memory while
+ * they run -- e.g. a host application that hands each plug-in a fixed
+ * device-memory budget and forbids calls to the allocator, or a long-running
+ * service that must not fail part-way because an allocation failed.
+ * Arguments, outputs and errors are those of rp_yields.  All device scratch
+ * (state vectors, singlet slices, Gram matrices, per-row bookkeeping,
+ * per-field tables, per-sample results) comes from one file-scope device array
+ * of 64 MiB (67108864 bytes) that every GPU loading the library holds until
+ * the process exits; no cudaMalloc/cudaFree or allocating routine is called.
+ * Rows are batched to fit the array; a workload whose fixed part plus one row
+ * does not fit is rejected with RP_EINVAL and a message giving the bytes it
+ * needs.  All calls share the array and find the previous call's contents in
+ * it (the call clears what must start at zero); calls that overlap on the GPU
+ * race on it.  The first call on a device looks up the array's address with
+ * that device current and should come before any stream capture.
+ * rp_stats.device_ms and the step timings are not measured (0). */
+rp_status rp_yields_static(rp_system* sys, int n_fields, const double* fields, int M,
+                           uint64_t seed, double t_max, const rp_options* opt, double* out,
+                           double* per_sample, rp_stats* stats);
+
 #ifdef __cplusplus
 }
 #endif

@@ -398,6 +398,10 @@ rp_status run_yields(rp_system* sys, int n_fields, const double* fields, int M, 
 
 }  // namespace
 
+namespace rp {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace rp
+
 extern "C" {
 
 const char* rp_version(void) { return "rp-gb300 0.1 (sm_103a)"; }

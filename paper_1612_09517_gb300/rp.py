@@ -85,6 +85,10 @@ SIGNATURES = [
                              C.c_void_p]),
     ("rp_init_states", C.c_int, [C.c_void_p, C.c_int, C.c_uint64, C.c_uint32, C.c_longlong,
                                  C.c_int, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
+    ("rp_yields_static", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_int,
+                                   C.c_uint64, C.c_double, C.POINTER(rp_options),
+                                   C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                   C.POINTER(rp_stats)]),
 ]
 
 
@@ -174,6 +178,25 @@ def rp_yields(h, fields, M, seed, t_max, opt=None, per_sample=False, Z=None):
     _check(LIB.rp_yields(h, nf, _dptr(fields), int(M), C.c_uint64(int(seed)), float(t_max),
                          C.byref(o), _dptr(out), _dptr(ps) if per_sample else None,
                          C.byref(stats)))
+    res = {"out": out[: nf * 5].reshape(nf, 5), "stats": stats.as_dict()}
+    if per_sample:
+        res["per_sample"] = ps[: nf * Mr * 3].reshape(nf, Mr, 3)
+    return res
+
+
+def rp_yields_static(h, fields, M, seed, t_max, opt=None, per_sample=False, Z=None):
+    """rp_yields with all device scratch in the library's fixed 64 MiB array
+    (for callers that must not allocate device memory while they run)."""
+    fields = np.ascontiguousarray(fields, dtype=np.float64).reshape(-1)
+    nf = fields.size
+    o = opt if opt is not None else rp_default_options()
+    out = np.zeros(max(nf * 5, 1))
+    Mr = Z if o.deterministic else M
+    ps = np.zeros(max(nf * Mr * 3, 1)) if per_sample else None
+    stats = rp_stats()
+    _check(LIB.rp_yields_static(h, nf, _dptr(fields), int(M), C.c_uint64(int(seed)),
+                                float(t_max), C.byref(o), _dptr(out),
+                                _dptr(ps) if per_sample else None, C.byref(stats)))
     res = {"out": out[: nf * 5].reshape(nf, 5), "stats": stats.as_dict()}
     if per_sample:
         res["per_sample"] = ps[: nf * Mr * 3].reshape(nf, Mr, 3)
