@@ -70,8 +70,8 @@ typedef struct rp_options {
   int precision;          /* RP_FP64 or RP_FP32: storage and arithmetic of the
                              state vectors; time integrals, Chebyshev
                              coefficients and averages are FP64 always */
-  int n_cheb;             /* Chebyshev terms per macro-step, multiple of 4 in [8, 96]
-                             (0: 64 FP64, 40 FP32) */
+  int n_cheb;             /* Chebyshev terms per macro-step, multiple of 4 in [8, 88]
+                             (0: 64 FP64, 88 FP32) */
   double tol;             /* truncation bound per macro-step (0: 1e-15 FP64, 1e-9 FP32) */
   int max_rows;           /* concurrent propagations (0: from free device memory) */
   int deterministic;      /* 1: trace over the Z basis states |S, M> (Eq. 14)

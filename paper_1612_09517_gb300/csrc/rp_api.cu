@@ -154,7 +154,7 @@ rp::LayoutDev make_layout(const rp::HostSystem& s) {
   return L;
 }
 
-int default_ncheb(int precision) { return precision == RP_FP64 ? 64 : 40; }
+int default_ncheb(int precision) { return precision == RP_FP64 ? 64 : 88; }
 double default_tol(int precision) { return precision == RP_FP64 ? 1e-15 : 1e-9; }
 
 struct Counter {
@@ -174,8 +174,8 @@ rp_status run_yields(rp_system* sys, int n_fields, const double* fields, int M, 
   cudaStream_t st = (cudaStream_t)o.stream;
   const int n_c = o.n_cheb > 0 ? o.n_cheb : default_ncheb(o.precision);
   const double tol = o.tol > 0 ? o.tol : default_tol(o.precision);
-  if (n_c % 4 != 0 || n_c < 8 || n_c > 96)
-    return fail(RP_EINVAL, "n_cheb must be a multiple of 4 in [8, 96]");
+  if (n_c % 4 != 0 || n_c < 8 || n_c > 88)
+    return fail(RP_EINVAL, "n_cheb must be a multiple of 4 in [8, 88]");
   const long long Mr = o.deterministic ? hs.Z : (long long)M;
   const long long Z = hs.Z;
 
@@ -195,7 +195,7 @@ rp_status run_yields(rp_system* sys, int n_fields, const double* fields, int M, 
   // rows from the memory budget
   const size_t vec_elems = (size_t)Z * 8;  // T per state vector
   const size_t per_row = (4 * vec_elems + (size_t)n_c * Z * 2) * sizeof(T) +
-                         (size_t)n_c * n_c * 2 * sizeof(double) + 256 + rp::kMaxNucDev * 20 * 8;
+                         256 + rp::kMaxNucDev * 20 * 8;
   long long rows_cap = o.max_rows > 0 ? o.max_rows : 0;
   if (rows_cap == 0) {
     size_t fr = 0, tot = 0;
@@ -238,7 +238,6 @@ rp_status run_yields(rp_system* sys, int n_fields, const double* fields, int M, 
     T* F1 = ar.get<T>((size_t)R * vec_elems);
     T* F2 = ar.get<T>((size_t)R * vec_elems);
     T* X = ar.get<T>((size_t)R * n_c * Z * 2);
-    double* G = ar.get<double>((size_t)R * n_c * n_c * 2);
     double* amps = ar.get<double>((size_t)R * rp::kMaxNucDev * 10 * 2);
     int* d_field = ar.get<int>(R);
     int* d_nmacro = ar.get<int>(R);
@@ -275,7 +274,6 @@ rp_status run_yields(rp_system* sys, int n_fields, const double* fields, int M, 
     ck(cudaMemcpyAsync(d_coef, coef.data(), coef.size() * sizeof(T), cudaMemcpyHostToDevice, st), "h2d coef");
     ck(cudaMemcpyAsync(d_W, W.data(), W.size() * sizeof(double), cudaMemcpyHostToDevice, st), "h2d W");
     h2d += (long long)(fdev.size() * sizeof(fdev[0]) + coef.size() * sizeof(T) + W.size() * sizeof(double));
-    launched(cnt, rp::launch_zero(G, (size_t)R * n_c * n_c * 2, st), "zero G");
 
     const rp::HamDev<T> H = make_ham<T>(hs);
     const rp::LayoutDev L = make_layout(hs);
@@ -348,9 +346,9 @@ rp_status run_yields(rp_system* sys, int n_fields, const double* fields, int M, 
         }
         step_bytes_all += bytes;
         row_terms += act * (long long)n_c;
-        launched(cnt, rp::launch_gram<T>(X, G, d_nmacro, k, rows, Z, n_c, st), "gram kernel");
-        launched(cnt, rp::launch_integrate(G, d_W, d_field, d_nmacro, k, rows, n_c, d_int, st),
-                 "integrate kernel");
+        launched(cnt, rp::launch_gram_integrate<T>(X, d_W, d_field, d_nmacro, k, rows, Z, n_c,
+                                                   d_int, st),
+                 "gram-integral kernel");
       }
       launched(cnt, rp::launch_norm<T>(S0, S1, d_nmacro, rows, Z, d_surv, st), "norm kernel");
       rp::RowsDev RD{d_field, d_nmacro, d_sample, d_out, d_int, d_surv};

@@ -26,47 +26,82 @@ __device__ __forceinline__ void rmac(Cx<T>& y, T g, const Cx<T>& q) {
   y.im = fma(g, q.im, y.im);
 }
 
-// Four complex values (the electron components of one nuclear configuration).
+// Four complex values (the electron components of one nuclear configuration):
+// 32 bytes in FP32, moved with one 256-bit access per thread (sm_100+), so a
+// warp reads or writes 1 KB contiguous per instruction; 64 bytes in FP64, two
+// 256-bit accesses.  Addresses are 32-byte aligned (buffers are 256-byte
+// aligned and a configuration is 32 or 64 bytes).
 __device__ __forceinline__ void load4(const float* p, Cx<float> (&a)[4]) {
-  const float4 u = __ldg(reinterpret_cast<const float4*>(p));
-  const float4 v = __ldg(reinterpret_cast<const float4*>(p) + 1);
-  a[0] = {u.x, u.y};
-  a[1] = {u.z, u.w};
-  a[2] = {v.x, v.y};
-  a[3] = {v.z, v.w};
+  asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(a[0].re), "=f"(a[0].im), "=f"(a[1].re), "=f"(a[1].im), "=f"(a[2].re),
+                 "=f"(a[2].im), "=f"(a[3].re), "=f"(a[3].im)
+               : "l"(p));
 }
 __device__ __forceinline__ void load4(const double* p, Cx<double> (&a)[4]) {
-  const double2* q = reinterpret_cast<const double2*>(p);
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    const double2 u = __ldg(q + e);
-    a[e] = {u.x, u.y};
-  }
+  asm("ld.global.nc.v4.f64 {%0,%1,%2,%3}, [%4];"
+               : "=d"(a[0].re), "=d"(a[0].im), "=d"(a[1].re), "=d"(a[1].im)
+               : "l"(p));
+  asm("ld.global.nc.v4.f64 {%0,%1,%2,%3}, [%4];"
+               : "=d"(a[2].re), "=d"(a[2].im), "=d"(a[3].re), "=d"(a[3].im)
+               : "l"(p + 4));
 }
 __device__ __forceinline__ void load4_rw(const float* p, Cx<float> (&a)[4]) {
-  const float4 u = reinterpret_cast<const float4*>(p)[0];
-  const float4 v = reinterpret_cast<const float4*>(p)[1];
-  a[0] = {u.x, u.y};
-  a[1] = {u.z, u.w};
-  a[2] = {v.x, v.y};
-  a[3] = {v.z, v.w};
+  asm("ld.global.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=f"(a[0].re), "=f"(a[0].im), "=f"(a[1].re), "=f"(a[1].im), "=f"(a[2].re),
+                 "=f"(a[2].im), "=f"(a[3].re), "=f"(a[3].im)
+               : "l"(p)
+               : "memory");
 }
 __device__ __forceinline__ void load4_rw(const double* p, Cx<double> (&a)[4]) {
-  const double2* q = reinterpret_cast<const double2*>(p);
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    const double2 u = q[e];
-    a[e] = {u.x, u.y};
-  }
+  asm("ld.global.v4.f64 {%0,%1,%2,%3}, [%4];"
+               : "=d"(a[0].re), "=d"(a[0].im), "=d"(a[1].re), "=d"(a[1].im)
+               : "l"(p)
+               : "memory");
+  asm("ld.global.v4.f64 {%0,%1,%2,%3}, [%4];"
+               : "=d"(a[2].re), "=d"(a[2].im), "=d"(a[3].re), "=d"(a[3].im)
+               : "l"(p + 4)
+               : "memory");
 }
 __device__ __forceinline__ void store4(float* p, const Cx<float> (&a)[4]) {
-  reinterpret_cast<float4*>(p)[0] = make_float4(a[0].re, a[0].im, a[1].re, a[1].im);
-  reinterpret_cast<float4*>(p)[1] = make_float4(a[2].re, a[2].im, a[3].re, a[3].im);
+  asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(a[0].re),
+               "f"(a[0].im), "f"(a[1].re), "f"(a[1].im), "f"(a[2].re), "f"(a[2].im), "f"(a[3].re),
+               "f"(a[3].im)
+               : "memory");
 }
 __device__ __forceinline__ void store4(double* p, const Cx<double> (&a)[4]) {
-  double2* q = reinterpret_cast<double2*>(p);
+  asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p), "d"(a[0].re), "d"(a[0].im),
+               "d"(a[1].re), "d"(a[1].im)
+               : "memory");
+  asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p + 4), "d"(a[2].re), "d"(a[2].im),
+               "d"(a[3].re), "d"(a[3].im)
+               : "memory");
+}
+
+// Shared-memory tile of a block's configurations in 16-byte planes: plane k
+// holds bytes [16k, 16k + 16) of every configuration, so each 16-byte access
+// of a warp is contiguous (no bank conflicts).
+template <typename T>
+struct Planes {
+  static constexpr int kPlanes = (int)(4 * sizeof(Cx<T>) / 16);  // 2 (FP32) or 4 (FP64)
+  static constexpr int kCx = 16 / (int)sizeof(Cx<T>);             // complex per plane entry
+};
+
+template <typename T>
+__device__ __forceinline__ void tile_put(Cx<T>* tile, int nthreads, int i, const Cx<T> (&a)[4]) {
+  constexpr int kc = Planes<T>::kCx;
 #pragma unroll
-  for (int e = 0; e < 4; ++e) q[e] = make_double2(a[e].re, a[e].im);
+  for (int k = 0; k < Planes<T>::kPlanes; ++k)
+#pragma unroll
+    for (int e = 0; e < kc; ++e) tile[((size_t)k * nthreads + i) * kc + e] = a[k * kc + e];
+}
+
+template <typename T>
+__device__ __forceinline__ void tile_get(const Cx<T>* tile, int nthreads, int i, Cx<T> (&a)[4]) {
+  constexpr int kc = Planes<T>::kCx;
+#pragma unroll
+  for (int k = 0; k < Planes<T>::kPlanes; ++k)
+#pragma unroll
+    for (int e = 0; e < kc; ++e) a[k * kc + e] = tile[((size_t)k * nthreads + i) * kc + e];
 }
 
 template <typename T>
@@ -103,10 +138,8 @@ __device__ __forceinline__ void apply_e2x2(Cx<T> (&y)[4], const Cx<T> (&q)[4], i
 // Partner contribution of nucleus p from configuration m + step * stride:
 // step = +1 uses c U_p (I_+ brings M-1 to M), step = -1 uses c U_p^dagger.
 template <typename T, bool ANISO>
-__device__ __forceinline__ void add_partner(Cx<T> (&y)[4], const T* c, long long mp, int rr,
-                                            const T* U, T coeff, bool up) {
-  Cx<T> q[4];
-  load4(c + mp * 8, q);
+__device__ __forceinline__ void add_partner_q(Cx<T> (&y)[4], const Cx<T> (&q)[4], int rr,
+                                              const T* U, T coeff, bool up) {
   if (!ANISO) {
     // isotropic: U = [[0, 0], [a/2, 0]], so only S_-I_+ / S_+I_- flip-flops
     const T g = coeff * U[4];
@@ -147,6 +180,14 @@ __device__ __forceinline__ void add_partner(Cx<T> (&y)[4], const T* c, long long
   }
 }
 
+template <typename T, bool ANISO>
+__device__ __forceinline__ void add_partner(Cx<T> (&y)[4], const T* c, unsigned mp, int rr,
+                                            const T* U, T coeff, bool up) {
+  Cx<T> q[4];
+  load4(c + (size_t)mp * 8, q);
+  add_partner_q<T, ANISO>(y, q, rr, U, coeff, up);
+}
+
 template <typename T>
 __device__ __forceinline__ void add_field(T (&b1)[3], T (&b2)[3], int rr, T M, const T* v) {
   if (rr == 0) {
@@ -166,75 +207,153 @@ __device__ __forceinline__ void add_field(T (&b1)[3], T (&b2)[3], int rr, T M, c
 //   MID:   phi_n = 2z - phi_{n-2}, acc += c_n phi_n,        X[n] = <S|phi_n>
 //   LAST:  as MID but phi_n is not stored (acc becomes psi at the end of the step)
 //   APPLY: next = s H' a - sh a   (used with s = 1, sh = i kbar/2 for H - iK)
+// The block (a power of two, at most 256 configurations) stages its own
+// configurations in shared memory: for the n_in innermost spin-1/2 nuclei
+// (stride 2^p < blockDim) the partner m XOR 2^p lies in the same block.
+// Configuration indices are 32-bit (Z <= 2^31); the nucleus loops are unrolled
+// with predicates so per-nucleus constants are fixed-offset parameter loads.
+constexpr int kStepThreads = 256;
+constexpr int kInnerBits = 8;  // log2(kStepThreads)
+
+// Isotropic flip-flop of a spin-1/2 nucleus: j = 0 (M = +1/2) takes the
+// partner through U (y_beta += g q_alpha), j = 1 through U^dagger
+// (y_alpha += g q_beta), g = a/2 on the electron of radical rr.
+template <typename T>
+__device__ __forceinline__ void iso_half(Cx<T> (&y)[4], const Cx<T> (&q)[4], int rr, unsigned j,
+                                         T g) {
+  const T gu = j ? T(0) : g, gd = j ? g : T(0);
+  if (rr == 0) {
+    rmac(y[0], gd, q[2]);
+    rmac(y[1], gd, q[3]);
+    rmac(y[2], gu, q[0]);
+    rmac(y[3], gu, q[1]);
+  } else {
+    rmac(y[0], gd, q[1]);
+    rmac(y[2], gd, q[3]);
+    rmac(y[1], gu, q[0]);
+    rmac(y[3], gu, q[2]);
+  }
+}
+
 template <typename T, bool ANISO>
-__global__ void __launch_bounds__(256) k_cheb_step(
+__device__ __forceinline__ void half_nucleus(Cx<T> (&y)[4], T (&b1)[3], T (&b2)[3],
+                                             const HamDev<T>& H, int p, unsigned j,
+                                             const Cx<T> (&q)[4]) {
+  const int rr = H.rad[p];
+  if (ANISO) {
+    add_field(b1, b2, rr, j ? T(-0.5) : T(0.5), H.v[p]);
+    add_partner_q<T, true>(y, q, rr, H.U[p], T(1), j == 0);
+  } else {
+    const T g = H.U[p][4];  // a/2
+    const T dz = j ? -g : g;  // M a with M = +-1/2
+    if (rr == 0) b1[2] += dz;
+    else b2[2] += dz;
+    iso_half(y, q, rr, j, g);
+  }
+}
+
+template <typename T, bool ANISO>
+__global__ void __launch_bounds__(kStepThreads, sizeof(T) == 4 ? 4 : 2) k_cheb_step(
     const HamDev<T> H, const FieldDev<T>* __restrict__ fields, const int* __restrict__ row_field,
     const int* __restrict__ row_nmacro, long long macro, const T* __restrict__ cur,
     const T* __restrict__ prev, T* __restrict__ next, T* __restrict__ acc, T* __restrict__ X,
-    const T* __restrict__ coef, int n_c, int n, int mode) {
-  const long long Z = H.Z;
-  const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const T* __restrict__ coef, int n_c, int n, int mode, int n_in) {
+  extern __shared__ __align__(16) unsigned char step_smem[];
+  Cx<T>* tile = reinterpret_cast<Cx<T>*>(step_smem);  // planes x blockDim x 16 B
+  const unsigned Z = (unsigned)H.Z;
+  const unsigned m = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
-  if (m >= Z) return;
   int f = 0;
   if (mode != MODE_APPLY) {
-    if (macro >= row_nmacro[r]) return;
+    if (macro >= row_nmacro[r]) return;  // the whole block: one row
     f = row_field[r];
   }
-  const FieldDev<T> F = fields[f];
-  const size_t vs = (size_t)Z * 8;
-  const T* c = cur + (size_t)r * vs;
+  const bool valid = m < Z;
+  const size_t row0 = (size_t)r * Z * 8;
+  const T* c = cur + row0;
 
   Cx<T> a[4];
-  load4(c + m * 8, a);
+  if (valid) {
+    load4(c + (size_t)m * 8, a);
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) a[e] = {T(0), T(0)};
+  }
+  tile_put(tile, blockDim.x, threadIdx.x, a);
+  __syncthreads();
+  if (!valid) return;  // no barrier below
+
   Cx<T> y[4];
 #pragma unroll
   for (int e = 0; e < 4; ++e) y[e] = {T(0), T(0)};
   T b1[3] = {T(0), T(0), T(0)}, b2[3] = {T(0), T(0), T(0)};
 
-  // spin-1/2 nuclei: digit j = bit p; exactly one partner
-  for (int p = 0; p < H.n_half; ++p) {
-    const int j = (int)((m >> p) & 1);
-    const long long mp = j ? m - H.stride[p] : m + H.stride[p];
-    const int rr = H.rad[p];
-    add_field(b1, b2, rr, j ? T(-0.5) : T(0.5), H.v[p]);
-    add_partner<T, ANISO>(y, c, mp, rr, H.U[p], T(1), j == 0);
+  // spin-1/2 nuclei inside the block: partner from shared memory
+#pragma unroll
+  for (int p = 0; p < kInnerBits; ++p) {
+    if (p < n_in) {
+      const unsigned j = (m >> p) & 1u;
+      Cx<T> q[4];
+      tile_get(tile, blockDim.x, threadIdx.x ^ (1u << p), q);
+      half_nucleus<T, ANISO>(y, b1, b2, H, p, j, q);
+    }
+  }
+  // spin-1/2 nuclei outside the block (only when blockDim = 256): global partner
+#pragma unroll
+  for (int p = kInnerBits; p < kMaxNucDev; ++p) {
+    if (p < H.n_half) {
+      const unsigned j = (m >> p) & 1u;
+      const unsigned mp = m ^ (1u << p);
+      Cx<T> q[4];
+      load4(c + (size_t)mp * 8, q);
+      half_nucleus<T, ANISO>(y, b1, b2, H, p, j, q);
+    }
   }
   // spin-1 nuclei: base-3 digits; partners +1 (j < 2) and -1 (j > 0), both sqrt 2
-  long long qd = m >> H.n_half;
+  unsigned qd = m >> H.n_half;
+  const T s2 = T(1.41421356237309504880);
+#pragma unroll 4
   for (int p = H.n_half; p < H.n_half + H.n_one; ++p) {
-    const int j = (int)(qd % 3);
-    qd /= 3;
+    const unsigned j = qd % 3u;
+    qd /= 3u;
     const int rr = H.rad[p];
-    add_field(b1, b2, rr, T(1 - j), H.v[p]);
-    const T s2 = T(1.41421356237309504880);
-    if (j < 2) add_partner<T, ANISO>(y, c, m + H.stride[p], rr, H.U[p], s2, true);
-    if (j > 0) add_partner<T, ANISO>(y, c, m - H.stride[p], rr, H.U[p], s2, false);
+    const unsigned st = (unsigned)H.stride[p];
+    if (ANISO) {
+      add_field(b1, b2, rr, T(1) - T(j), H.v[p]);
+    } else {
+      const T dz = (T(1) - T(j)) * H.v[p][2];
+      if (rr == 0) b1[2] += dz;
+      else b2[2] += dz;
+    }
+    if (j < 2u) add_partner<T, ANISO>(y, c, m + st, rr, H.U[p], s2, true);
+    if (j > 0u) add_partner<T, ANISO>(y, c, m - st, rr, H.U[p], s2, false);
   }
   // any other spin
   for (int p = H.n_half + H.n_one; p < H.n_nuc; ++p) {
-    const int d = H.d[p];
-    const int j = (int)(qd % d);
+    const unsigned d = (unsigned)H.d[p];
+    const unsigned j = qd % d;
     qd /= d;
     const int rr = H.rad[p];
+    const unsigned st = (unsigned)H.stride[p];
     const T I = T(0.5) * T(d - 1), M = I - T(j);
     add_field(b1, b2, rr, M, H.v[p]);
-    if (j < d - 1)
-      add_partner<T, ANISO>(y, c, m + H.stride[p], rr, H.U[p], sqrt(I * (I + 1) - M * (M - 1)), true);
-    if (j > 0)
-      add_partner<T, ANISO>(y, c, m - H.stride[p], rr, H.U[p], sqrt(I * (I + 1) - M * (M + 1)), false);
+    if (j + 1u < d)
+      add_partner<T, ANISO>(y, c, m + st, rr, H.U[p], sqrt(I * (I + 1) - M * (M - 1)), true);
+    if (j > 0u)
+      add_partner<T, ANISO>(y, c, m - st, rr, H.U[p], sqrt(I * (I + 1) - M * (M + 1)), false);
   }
 
-  // electron block: omega (S1z + S2z) + 2J S1.S2 - i kappa (2 P_S - 1)
+  // electron block: omega (S1z + S2z) + 2J S1.S2 - i kappa (2 P_S - 1), plus the
+  // diagonal-in-m hyperfine part (S1 . b1) x 1 + 1 x (S2 . b2), b_i = sum_k M_k A_k e_z
+  const FieldDev<T> F = fields[f];
   const T w = F.omega, Je = H.Je, kp = H.kappa, hJ = T(0.5) * Je;
-  cmac(y[0], w + hJ, kp, a[0]);
-  cmac(y[1], -hJ, T(0), a[1]);
-  cmac(y[1], Je, kp, a[2]);
-  cmac(y[2], Je, kp, a[1]);
-  cmac(y[2], -hJ, T(0), a[2]);
-  cmac(y[3], -w + hJ, kp, a[3]);
-  // diagonal-in-m hyperfine part: (S1 . b1) x 1 + 1 x (S2 . b2), b_i = sum_k M_k A_k e_z
-  {
+  if (ANISO) {
+    cmac(y[0], w + hJ, kp, a[0]);
+    cmac(y[1], -hJ, T(0), a[1]);
+    cmac(y[1], Je, kp, a[2]);
+    cmac(y[2], Je, kp, a[1]);
+    cmac(y[2], -hJ, T(0), a[2]);
+    cmac(y[3], -w + hJ, kp, a[3]);
     const T h = T(0.5);
 #pragma unroll
     for (int e2 = 0; e2 < 2; ++e2) {
@@ -252,6 +371,14 @@ __global__ void __launch_bounds__(256) k_cheb_step(
       cmac(y[2 * e1 + 1], h * b2[0], h * b2[1], lo);
       cmac(y[2 * e1 + 1], -h * b2[2], T(0), hi);
     }
+  } else {
+    const T sp = T(0.5) * (b1[2] + b2[2]), sm = T(0.5) * (b1[2] - b2[2]);
+    cmac(y[0], w + hJ + sp, kp, a[0]);
+    cmac(y[1], -hJ + sm, T(0), a[1]);
+    cmac(y[1], Je, kp, a[2]);
+    cmac(y[2], Je, kp, a[1]);
+    cmac(y[2], -hJ - sm, T(0), a[2]);
+    cmac(y[3], -w + hJ - sp, kp, a[3]);
   }
   // z = s y - sh a
   Cx<T> z[4];
@@ -260,7 +387,7 @@ __global__ void __launch_bounds__(256) k_cheb_step(
     z[e].re = F.s * y[e].re - (F.sh_re * a[e].re - F.sh_im * a[e].im);
     z[e].im = F.s * y[e].im - (F.sh_re * a[e].im + F.sh_im * a[e].re);
   }
-  const size_t off = (size_t)r * vs + (size_t)m * 8;
+  const size_t off = row0 + (size_t)m * 8;
   if (mode == MODE_APPLY) {
     store4(next + off, z);
     return;
@@ -300,26 +427,48 @@ __global__ void __launch_bounds__(256) k_cheb_step(
   store_singlet(xr + ((size_t)n * Z + m) * 2, ph);
 }
 
-// Singlet Gram G[r][n][m] += sum_z conj(x_n(z)) x_m(z) over a slice of z, for
-// 4x4 tiles (n, m) with n <= m.  Products and per-chunk sums in T, running
-// sums in FP64, one FP64 atomic per entry per CTA.
-constexpr int kGramZC = 32;
+template <int NT>
+__device__ double block_sum(double v, double* sh) {
+  sh[threadIdx.x] = v;
+  __syncthreads();
+#pragma unroll
+  for (int s = NT / 2; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  return sh[0];
+}
+
+// Exact time integral of one macro-step (Eq. 20 / Eq. 22 over [t, t + h]):
+//   integral[r] += sum_nm W_nm G_nm,  G_nm = sum_z conj(x_n(z)) x_m(z),
+// where x_n = <S|phi_n> are the singlet slices stored by the step kernel.
+// Each CTA forms the partial Gram of a slice of z for 4x4 tiles (n, m), n <= m
+// (chunks of z staged z-major in shared memory; `groups` thread groups split
+// each chunk), contracts it with W of the row's field in FP64 (factor 2 for
+// n < m: W and G are Hermitian) and adds one scalar to integral[r].  Sums run
+// in T within a chunk and in a second T accumulator across chunks.
+constexpr int kGramThreads = 256;
 
 template <typename T>
-__global__ void k_gram(const T* __restrict__ X, double* __restrict__ G,
-                       const int* __restrict__ row_nmacro, long long macro, long long Z, int n_c,
-                       long long z_per_cta) {
+__global__ void __launch_bounds__(kGramThreads) k_gram_integrate(
+    const T* __restrict__ X, const double* __restrict__ W, const int* __restrict__ row_field,
+    const int* __restrict__ row_nmacro, long long macro, long long Z, int n_c, int tiles,
+    int groups, int zc, long long z_per_cta, double* __restrict__ integral) {
   const int r = blockIdx.y;
   if (macro >= row_nmacro[r]) return;
   const long long z0 = (long long)blockIdx.x * z_per_cta;
   const long long z1 = min(Z, z0 + z_per_cta);
   if (z0 >= z1) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  Cx<T>* sx = reinterpret_cast<Cx<T>*>(smem_raw);  // [n_c][kGramZC]
-  const int nt = n_c / 4;
-  int ti = -1, tj = -1;
+  const int ldn = n_c + 2;  // row stride of the z-major tile (16-byte multiple)
+  Cx<T>* sx = reinterpret_cast<Cx<T>*>(smem_raw);  // [zc][ldn]
+  const int tid = threadIdx.x;
+  const int g = tid / tiles, t = tid % tiles;
+  const bool active = g < groups;
+  int ti = 0, tj = 0;
   {
-    int k = threadIdx.x;
+    const int nt = n_c / 4;
+    int k = t;
     for (int i = 0; i < nt; ++i) {
       const int cnt = nt - i;
       if (k < cnt) {
@@ -330,37 +479,38 @@ __global__ void k_gram(const T* __restrict__ X, double* __restrict__ G,
       k -= cnt;
     }
   }
-  double ar[4][4], ai[4][4];
+  T a2r[4][4], a2i[4][4];
 #pragma unroll
   for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) ar[i][j] = ai[i][j] = 0.0;
+    for (int j = 0; j < 4; ++j) a2r[i][j] = a2i[i][j] = T(0);
   const T* Xr = X + (size_t)r * n_c * Z * 2;
-  for (long long zc = z0; zc < z1; zc += kGramZC) {
+  for (long long c0 = z0; c0 < z1; c0 += zc) {
     __syncthreads();
-    for (int idx = threadIdx.x; idx < n_c * kGramZC; idx += blockDim.x) {
-      const int nn = idx / kGramZC, zz = idx % kGramZC;
-      const long long z = zc + zz;
+    for (int idx = tid; idx < n_c * zc; idx += blockDim.x) {
+      const int nn = idx / zc, zz = idx - nn * zc;
+      const long long z = c0 + zz;
       Cx<T> v = {T(0), T(0)};
       if (z < z1) {
         v.re = Xr[((size_t)nn * Z + z) * 2];
         v.im = Xr[((size_t)nn * Z + z) * 2 + 1];
       }
-      sx[nn * kGramZC + zz] = v;
+      sx[zz * ldn + nn] = v;
     }
     __syncthreads();
-    if (ti >= 0) {
+    if (active) {
       T pr[4][4], pi[4][4];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) pr[i][j] = pi[i][j] = T(0);
-      for (int zz = 0; zz < kGramZC; ++zz) {
+      for (int zz = g; zz < zc; zz += groups) {
+        const Cx<T>* row = sx + zz * ldn;
         Cx<T> xi[4], xj[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          xi[i] = sx[(4 * ti + i) * kGramZC + zz];
-          xj[i] = sx[(4 * tj + i) * kGramZC + zz];
+          xi[i] = row[4 * ti + i];
+          xj[i] = row[4 * tj + i];
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i)
@@ -374,62 +524,47 @@ __global__ void k_gram(const T* __restrict__ X, double* __restrict__ G,
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          ar[i][j] += (double)pr[i][j];
-          ai[i][j] += (double)pi[i][j];
+          a2r[i][j] += pr[i][j];
+          a2i[i][j] += pi[i][j];
         }
     }
   }
-  if (ti < 0) return;
-  double* Gr = G + (size_t)r * n_c * n_c * 2;
-#pragma unroll
-  for (int i = 0; i < 4; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int nn = 4 * ti + i, mm = 4 * tj + j;
-      if (nn <= mm) {
-        atomicAdd(Gr + ((size_t)nn * n_c + mm) * 2, ar[i][j]);
-        atomicAdd(Gr + ((size_t)nn * n_c + mm) * 2 + 1, ai[i][j]);
-      }
-    }
-}
-
-template <int NT>
-__device__ double block_sum(double v, double* sh) {
-  sh[threadIdx.x] = v;
+  // combine the thread groups of each tile through shared memory
   __syncthreads();
+  T* red = reinterpret_cast<T*>(smem_raw);  // [groups][tiles][32]
+  if (active && groups > 1) {
 #pragma unroll
-  for (int s = NT / 2; s > 0; s >>= 1) {
-    if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-    __syncthreads();
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        red[((size_t)g * tiles + t) * 32 + 2 * (4 * i + j)] = a2r[i][j];
+        red[((size_t)g * tiles + t) * 32 + 2 * (4 * i + j) + 1] = a2i[i][j];
+      }
   }
-  return sh[0];
-}
-
-// integral[r] += sum_nm W_nm G_nm = sum_n W_nn G_nn + 2 Re sum_{n<m} W_nm G_nm; G := 0.
-__global__ void __launch_bounds__(256) k_integrate(double* __restrict__ G,
-                                                   const double* __restrict__ W,
-                                                   const int* __restrict__ row_field,
-                                                   const int* __restrict__ row_nmacro,
-                                                   long long macro, int n_c,
-                                                   double* __restrict__ integral) {
-  __shared__ double sh[256];
-  const int r = blockIdx.x;
-  if (macro >= row_nmacro[r]) return;
-  const int f = row_field[r];
-  double* Gr = G + (size_t)r * n_c * n_c * 2;
-  const double* Wf = W + (size_t)f * n_c * n_c * 2;
+  __syncthreads();
   double s = 0.0;
-  for (int idx = threadIdx.x; idx < n_c * n_c; idx += blockDim.x) {
-    const int nn = idx / n_c, mm = idx % n_c;
-    if (nn > mm) continue;
-    const double gr = Gr[2 * idx], gi = Gr[2 * idx + 1];
-    const double v = Wf[2 * idx] * gr - Wf[2 * idx + 1] * gi;
-    s += (nn == mm) ? v : 2.0 * v;
-    Gr[2 * idx] = 0.0;
-    Gr[2 * idx + 1] = 0.0;
+  if (active && g == 0) {
+    const double* Wf = W + (size_t)row_field[r] * n_c * n_c * 2;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int nn = 4 * ti + i, mm = 4 * tj + j;
+        if (nn > mm) continue;
+        double gr = (double)a2r[i][j], gi = (double)a2i[i][j];
+        for (int q = 1; q < groups; ++q) {
+          gr += (double)red[((size_t)q * tiles + t) * 32 + 2 * (4 * i + j)];
+          gi += (double)red[((size_t)q * tiles + t) * 32 + 2 * (4 * i + j) + 1];
+        }
+        const size_t w = ((size_t)nn * n_c + mm) * 2;
+        const double v = Wf[w] * gr - Wf[w + 1] * gi;
+        s += (nn == mm) ? v : 2.0 * v;
+      }
   }
-  const double tot = block_sum<256>(s, sh);
-  if (threadIdx.x == 0) integral[r] += tot;
+  __syncthreads();
+  double* sh = reinterpret_cast<double*>(smem_raw);
+  const double tot = block_sum<kGramThreads>(s, sh);
+  if (tid == 0) atomicAdd(integral + r, tot);
 }
 
 // survival[r] += |psi|^2 over a slice; psi of row r sits in S[n_macro % 2].
@@ -631,41 +766,45 @@ cudaError_t launch_step(const HamDev<T>& H, const FieldDev<T>* fields, const int
                         const T* prev, T* next, T* acc, T* X, const T* coef, int n_c, int n,
                         int mode, cudaStream_t st) {
   if (rows == 0) return cudaSuccess;
-  const int b = H.Z >= 256 ? 256 : (int)((H.Z + 31) / 32 * 32);
+  // power-of-two blocks so that m XOR 2^p stays inside the block for 2^p < b
+  int b = 32;
+  while (b < kStepThreads && b < H.Z) b *= 2;
+  int lb = 0;
+  while ((1 << (lb + 1)) <= b) ++lb;
+  const int n_in = H.n_half < lb ? H.n_half : lb;
+  const size_t smem = (size_t)b * 4 * sizeof(Cx<T>);
   dim3 grid(grid1(H.Z, b), rows);
   if (H.aniso)
-    k_cheb_step<T, true><<<grid, b, 0, st>>>(H, fields, row_field, row_nmacro, macro, cur, prev,
-                                             next, acc, X, coef, n_c, n, mode);
+    k_cheb_step<T, true><<<grid, b, smem, st>>>(H, fields, row_field, row_nmacro, macro, cur, prev,
+                                                next, acc, X, coef, n_c, n, mode, n_in);
   else
-    k_cheb_step<T, false><<<grid, b, 0, st>>>(H, fields, row_field, row_nmacro, macro, cur, prev,
-                                              next, acc, X, coef, n_c, n, mode);
+    k_cheb_step<T, false><<<grid, b, smem, st>>>(H, fields, row_field, row_nmacro, macro, cur,
+                                                 prev, next, acc, X, coef, n_c, n, mode, n_in);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_gram(const T* X, double* G, const int* row_nmacro, long long macro, int rows,
-                        long long Z, int n_c, cudaStream_t st) {
+cudaError_t launch_gram_integrate(const T* X, const double* W, const int* row_field,
+                                  const int* row_nmacro, long long macro, int rows, long long Z,
+                                  int n_c, double* integral, cudaStream_t st) {
   if (rows == 0) return cudaSuccess;
   const int nt = n_c / 4;
   const int tiles = nt * (nt + 1) / 2;
-  const int b = (tiles + 31) / 32 * 32;
-  // aim for ~4 CTAs per SM over all rows, at least one chunk per CTA
-  long long target = (4LL * 152 + rows - 1) / rows;
-  long long chunks = (Z + kGramZC - 1) / kGramZC;
-  long long split = target < 1 ? 1 : (target > chunks ? chunks : target);
-  long long zper = (chunks + split - 1) / split * kGramZC;
-  split = (Z + zper - 1) / zper;
-  const size_t smem = (size_t)n_c * kGramZC * sizeof(Cx<T>);
-  dim3 grid((unsigned)split, rows);
-  k_gram<T><<<grid, b, smem, st>>>(X, G, row_nmacro, macro, Z, n_c, zper);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_integrate(double* G, const double* W, const int* row_field,
-                             const int* row_nmacro, long long macro, int rows, int n_c,
-                             double* integral, cudaStream_t st) {
-  if (rows == 0) return cudaSuccess;
-  k_integrate<<<rows, 256, 0, st>>>(G, W, row_field, row_nmacro, macro, n_c, integral);
+  const int groups = tiles >= kGramThreads ? 1 : kGramThreads / tiles;
+  const int zc = sizeof(T) == 4 ? 32 : 16;
+  const long long z_per_cta = 1024;
+  const size_t tile_b = (size_t)zc * (n_c + 2) * sizeof(Cx<T>);
+  const size_t red_b = (size_t)groups * tiles * 32 * sizeof(T);
+  size_t smem = tile_b > red_b ? tile_b : red_b;
+  if (smem < kGramThreads * sizeof(double)) smem = kGramThreads * sizeof(double);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_gram_integrate<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  dim3 grid((unsigned)((Z + z_per_cta - 1) / z_per_cta), rows);
+  k_gram_integrate<T><<<grid, kGramThreads, smem, st>>>(X, W, row_field, row_nmacro, macro, Z, n_c,
+                                                        tiles, groups, zc, z_per_cta, integral);
   return cudaGetLastError();
 }
 
@@ -711,10 +850,12 @@ template cudaError_t launch_step<double>(const HamDev<double>&, const FieldDev<d
                                          const int*, const int*, long long, int, const double*,
                                          const double*, double*, double*, double*, const double*,
                                          int, int, int, cudaStream_t);
-template cudaError_t launch_gram<float>(const float*, double*, const int*, long long, int,
-                                        long long, int, cudaStream_t);
-template cudaError_t launch_gram<double>(const double*, double*, const int*, long long, int,
-                                         long long, int, cudaStream_t);
+template cudaError_t launch_gram_integrate<float>(const float*, const double*, const int*,
+                                                  const int*, long long, int, long long, int,
+                                                  double*, cudaStream_t);
+template cudaError_t launch_gram_integrate<double>(const double*, const double*, const int*,
+                                                   const int*, long long, int, long long, int,
+                                                   double*, cudaStream_t);
 template cudaError_t launch_norm<float>(const float*, const float*, const int*, int, long long,
                                         double*, cudaStream_t);
 template cudaError_t launch_norm<double>(const double*, const double*, const int*, int, long long,

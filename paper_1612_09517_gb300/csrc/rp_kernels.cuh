@@ -72,13 +72,12 @@ cudaError_t launch_step(const HamDev<T>& H, const FieldDev<T>* fields, const int
                         const T* prev, T* next, T* acc, T* X, const T* coef, int n_c, int n,
                         int mode, cudaStream_t st);
 
+// integral[r] += sum_nm W_nm <x_n|x_m> for the macro-step just finished
+// (x_n = singlet slices X[r][n], W per field); one FP64 atomic per CTA.
 template <typename T>
-cudaError_t launch_gram(const T* X, double* G, const int* row_nmacro, long long macro, int rows,
-                        long long Z, int n_c, cudaStream_t st);
-
-cudaError_t launch_integrate(double* G, const double* W, const int* row_field,
-                             const int* row_nmacro, long long macro, int rows, int n_c,
-                             double* integral, cudaStream_t st);
+cudaError_t launch_gram_integrate(const T* X, const double* W, const int* row_field,
+                                  const int* row_nmacro, long long macro, int rows, long long Z,
+                                  int n_c, double* integral, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_norm(const T* S0, const T* S1, const int* row_nmacro, int rows, long long Z,

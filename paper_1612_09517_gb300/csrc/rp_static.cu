@@ -155,10 +155,10 @@ rp_status run_static(const rp::HostSystem& hs, int n_fields, const double* field
                      uint64_t seed, double t_max, const rp_options& o, double* out,
                      double* per_sample, rp_stats* stats, unsigned char* scratch) {
   cudaStream_t st = (cudaStream_t)o.stream;
-  const int n_c = o.n_cheb > 0 ? o.n_cheb : (o.precision == RP_FP64 ? 64 : 40);
+  const int n_c = o.n_cheb > 0 ? o.n_cheb : (o.precision == RP_FP64 ? 64 : 88);
   const double tol = o.tol > 0 ? o.tol : (o.precision == RP_FP64 ? 1e-15 : 1e-9);
-  if (n_c % 4 != 0 || n_c < 8 || n_c > 96)
-    return sfail(RP_EINVAL, "n_cheb must be a multiple of 4 in [8, 96]");
+  if (n_c % 4 != 0 || n_c < 8 || n_c > 88)
+    return sfail(RP_EINVAL, "n_cheb must be a multiple of 4 in [8, 88]");
   const long long Mr = o.deterministic ? hs.Z : (long long)M;
   const long long Z = hs.Z;
   std::vector<rp::FieldPlan> plans(n_fields);
@@ -180,7 +180,7 @@ rp_status run_static(const rp::HostSystem& hs, int n_fields, const double* field
                        up256((size_t)n_fields * n_c * n_c * 2 * sizeof(double));
   auto rows_bytes = [&](size_t R) {
     return 4 * up256(R * vec * sizeof(T)) + up256(R * n_c * Z * 2 * sizeof(T)) +
-           up256(R * n_c * n_c * 2 * sizeof(double)) + up256(R * rp::kMaxNucDev * 20 * sizeof(double)) +
+           up256(R * rp::kMaxNucDev * 20 * sizeof(double)) +
            2 * up256(R * sizeof(int)) + 2 * up256(R * sizeof(long long)) + up256(2 * R * sizeof(double));
   };
   if (fixed + rows_bytes(1) > kStaticScratchBytes)
@@ -201,7 +201,6 @@ rp_status run_static(const rp::HostSystem& hs, int n_fields, const double* field
   T* F1 = b.get<T>(R * vec);
   T* F2 = b.get<T>(R * vec);
   T* X = b.get<T>(R * n_c * Z * 2);
-  double* G = b.get<double>(R * n_c * n_c * 2);
   double* amps = b.get<double>(R * rp::kMaxNucDev * 20);
   int* d_field = b.get<int>(R);
   int* d_nmacro = b.get<int>(R);
@@ -237,8 +236,6 @@ rp_status run_static(const rp::HostSystem& hs, int n_fields, const double* field
   sck(cudaMemcpyAsync(d_coef, coef.data(), coef.size() * sizeof(T), cudaMemcpyHostToDevice, st), "h2d");
   sck(cudaMemcpyAsync(d_W, W.data(), W.size() * sizeof(double), cudaMemcpyHostToDevice, st), "h2d");
   h2d += (long long)(fdev.size() * sizeof(fdev[0]) + coef.size() * sizeof(T) + W.size() * sizeof(double));
-  // the array keeps the previous call's contents: the Gram must start at zero
-  L1(rp::launch_zero(G, R * n_c * n_c * 2, st), "zero Gram");
 
   const rp::HamDev<T> H = ham_of<T>(hs);
   const rp::LayoutDev L = layout_of(hs);
@@ -283,8 +280,8 @@ rp_status run_static(const rp::HostSystem& hs, int n_fields, const double* field
         steps++;
       }
       row_terms += act * n_c;
-      L1(rp::launch_gram<T>(X, G, d_nmacro, k, rows, Z, n_c, st), "gram kernel");
-      L1(rp::launch_integrate(G, d_W, d_field, d_nmacro, k, rows, n_c, d_int, st), "integrate kernel");
+      L1(rp::launch_gram_integrate<T>(X, d_W, d_field, d_nmacro, k, rows, Z, n_c, d_int, st),
+         "gram-integral kernel");
     }
     L1(rp::launch_norm<T>(S0, S1, d_nmacro, rows, Z, d_surv, st), "norm kernel");
     rp::RowsDev RD{d_field, d_nmacro, d_sample, d_out, d_int, d_surv};
