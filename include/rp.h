@@ -184,6 +184,20 @@ rp_status rp_yields(rp_system* sys, int n_fields, const double* fields, int M, u
                     double t_max, const rp_options* opt, double* out, double* per_sample,
                     rp_stats* stats);
 
+/* Yields over a field sweep to a target standard error (Eq. 23) at every field
+ * (the "SE <= target on the whole curve" criterion; Eqs. 18, 20, 22).
+ * Each field first gets M_min coherent-state samples; then, in rounds, each
+ * field whose standard error of Phi_S is above se_target gets the samples its
+ * measured spread asks for, ceil(1.15 sigma_f^2 / se_target^2) + 1, capped at
+ * M_max.  Sample s uses the same directions at every field.  All rounds run
+ * on one pool of rows that are refilled as propagations finish.
+ *   out     [n_fields * 5] host: Phi_S, Phi_T, SE_S, SE_T, mean survival
+ *   M_used  [n_fields] host or NULL: samples used per field
+ * opt->deterministic must be 0.  Errors as rp_yields. */
+rp_status rp_yields_converged(rp_system* sys, int n_fields, const double* fields, double se_target,
+                              int M_min, int M_max, uint64_t seed, double t_max,
+                              const rp_options* opt, double* out, int* M_used, rp_stats* stats);
+
 /* y = (H - iK) x for n_vec state vectors in the layout above, field B (mT);
  * x_dev and y_dev are device arrays of n_vec * 4Z complex values in the
  * precision given, and must not overlap.  Stream as in rp_options (may be

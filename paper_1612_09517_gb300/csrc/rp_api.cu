@@ -157,14 +157,295 @@ rp::LayoutDev make_layout(const rp::HostSystem& s) {
 int default_ncheb(int precision) { return precision == RP_FP64 ? 64 : 88; }
 double default_tol(int precision) { return precision == RP_FP64 ? 1e-15 : 1e-9; }
 
-struct Counter {
-  long long launches = 0, step_launches = 0;
+// One work item: a (field, sample) propagation over the whole horizon.
+struct Item {
+  int field;
+  long long sample;  // Philox sample index, or basis index when deterministic
+  long long out;     // slot in the per-sample output array
+  int n_macro;       // macro-steps of its field's plan
 };
 
-inline void launched(Counter& c, cudaError_t e, const char* what) {
-  ck(e, what);
-  c.launches++;
+// Runs lists of work items on a pool of R rows: every row propagates one item
+// through its macro-steps; when an item finishes, the row's survival and
+// yields are written and the row takes the next item at the next macro-step
+// (the schedule is known on the host from the per-field plans, so no
+// device-to-host traffic is needed to refill).
+template <typename T>
+class YieldEngine {
+ public:
+  YieldEngine(const rp::HostSystem& hs, const rp_options& o, int n_c, cudaStream_t st, Arena& ar)
+      : hs_(hs), o_(o), n_c_(n_c), st_(st), ar_(ar), H_(make_ham<T>(hs)), L_(make_layout(hs)) {}
+
+  long long launches = 0, step_launches = 0, row_terms = 0, h2d = 0;
+  double step_bytes_all = 0.0;
+  std::vector<cudaEvent_t> pev;
+  std::vector<double> pev_bytes;
+  std::vector<long long> pev_launches;
+
+  ~YieldEngine() {
+    for (auto e : pev) cudaEventDestroy(e);
+  }
+
+  void set_fields(const std::vector<rp::FieldPlan>& plans) {
+    const int nf = (int)plans.size();
+    d_fdev_ = ar_.get<rp::FieldDev<T>>(nf);
+    d_coef_ = ar_.get<T>((size_t)nf * n_c_ * 2);
+    d_W_ = ar_.get<double>((size_t)nf * n_c_ * n_c_ * 2);
+    std::vector<rp::FieldDev<T>> fdev(nf);
+    std::vector<T> coef((size_t)nf * n_c_ * 2);
+    std::vector<double> W((size_t)nf * n_c_ * n_c_ * 2);
+    for (int f = 0; f < nf; ++f) {
+      const rp::FieldPlan& P = plans[f];
+      fdev[f].omega = (T)P.omega;
+      fdev[f].s = (T)(1.0 / P.dE);
+      fdev[f].sh_re = (T)(P.E_c / P.dE);
+      fdev[f].sh_im = (T)0;
+      for (int n = 0; n < n_c_; ++n) {
+        coef[((size_t)f * n_c_ + n) * 2] = (T)P.coef[n].real();
+        coef[((size_t)f * n_c_ + n) * 2 + 1] = (T)P.coef[n].imag();
+      }
+      for (size_t i = 0; i < (size_t)n_c_ * n_c_; ++i) {
+        W[((size_t)f * n_c_ * n_c_ + i) * 2] = P.W[i].real();
+        W[((size_t)f * n_c_ * n_c_ + i) * 2 + 1] = P.W[i].imag();
+      }
+    }
+    ck(cudaMemcpyAsync(d_fdev_, fdev.data(), fdev.size() * sizeof(fdev[0]), cudaMemcpyHostToDevice, st_), "h2d fields");
+    ck(cudaMemcpyAsync(d_coef_, coef.data(), coef.size() * sizeof(T), cudaMemcpyHostToDevice, st_), "h2d coef");
+    ck(cudaMemcpyAsync(d_W_, W.data(), W.size() * sizeof(double), cudaMemcpyHostToDevice, st_), "h2d W");
+    h2d += (long long)(fdev.size() * sizeof(fdev[0]) + coef.size() * sizeof(T) + W.size() * sizeof(double));
+  }
+
+  static size_t row_bytes(long long Z, int n_c) {
+    return (4 * (size_t)Z * 8 + (size_t)n_c * Z * 2) * sizeof(T) + 256 + rp::kMaxNucDev * 20 * 8;
+  }
+
+  void alloc_rows(int R) {
+    R_ = R;
+    const size_t vec = (size_t)hs_.Z * 8;
+    S0_ = ar_.get<T>((size_t)R * vec);
+    S1_ = ar_.get<T>((size_t)R * vec);
+    F1_ = ar_.get<T>((size_t)R * vec);
+    F2_ = ar_.get<T>((size_t)R * vec);
+    X_ = ar_.get<T>((size_t)R * n_c_ * hs_.Z * 2);
+    amps_ = ar_.get<double>((size_t)R * rp::kMaxNucDev * 10 * 2);
+    rows_.field = ar_.get<int>(R);
+    rows_.win = ar_.get<int2>(R);
+    rows_.sample = ar_.get<long long>(R);
+    rows_.out = ar_.get<long long>(R);
+    rows_.flag = ar_.get<int>(R);
+    rows_.integral = ar_.get<double>(2 * (size_t)R);
+    rows_.survival = rows_.integral + R;
+  }
+
+  void run(const std::vector<Item>& items, double* d_ps) {
+    const int R = R_;
+    const long long n_items = (long long)items.size();
+    std::vector<int> h_field(R, 0), h_flag(R, 0);
+    std::vector<int2> h_win(R, make_int2(0, 0));
+    std::vector<long long> h_sample(R, 0), h_out(R, 0);
+    long long next = 0;
+    int live = 0;
+    auto assign = [&](int r, int k) {
+      const Item& it = items[next++];
+      h_field[r] = it.field;
+      h_win[r] = make_int2(k, k + it.n_macro);
+      h_sample[r] = it.sample;
+      h_out[r] = it.out;
+      h_flag[r] = 1;
+    };
+    auto upload_rows = [&]() {
+      ck(cudaMemcpyAsync(rows_.field, h_field.data(), R * sizeof(int), cudaMemcpyHostToDevice, st_), "h2d rows");
+      ck(cudaMemcpyAsync(rows_.win, h_win.data(), R * sizeof(int2), cudaMemcpyHostToDevice, st_), "h2d rows");
+      ck(cudaMemcpyAsync(rows_.sample, h_sample.data(), R * sizeof(long long), cudaMemcpyHostToDevice, st_), "h2d rows");
+      ck(cudaMemcpyAsync(rows_.out, h_out.data(), R * sizeof(long long), cudaMemcpyHostToDevice, st_), "h2d rows");
+      ck(cudaMemcpyAsync(rows_.flag, h_flag.data(), R * sizeof(int), cudaMemcpyHostToDevice, st_), "h2d rows");
+      h2d += (long long)R * (2 * sizeof(int) + sizeof(int2) + 2 * sizeof(long long));
+    };
+    auto init_flagged = [&]() {
+      if (!o_.deterministic)
+        launched(rp::launch_coherent_amps(L_, rows_.sample, rows_.flag, R, seed_, o_.pair_id, amps_,
+                                          nullptr, st_), "coherent amplitudes");
+      launched(rp::launch_init_state<T>(L_, amps_, rows_.sample, rows_.flag, rows_.win, R,
+                                        o_.deterministic, S0_, S1_, rows_.integral,
+                                        rows_.survival, st_), "initial states");
+    };
+    for (int r = 0; r < R && next < n_items; ++r) {
+      assign(r, 0);
+      ++live;
+    }
+    upload_rows();
+    init_flagged();
+    const double vbytes = (double)hs_.Z * 8 * sizeof(T);
+    for (int k = 0; live > 0; ++k) {
+      long long act = 0;
+      for (int r = 0; r < R; ++r) act += (h_win[r].x <= k && k < h_win[r].y) ? 1 : 0;
+      T* Sb[2] = {S0_, S1_};
+      T* P = Sb[k & 1];
+      T* Q = Sb[(k + 1) & 1];
+      T* phi[3] = {P, F1_, F2_};
+      if (o_.profile) {
+        cudaEvent_t a, b;
+        ck(cudaEventCreate(&a), "cudaEventCreate");
+        pev.push_back(a);
+        ck(cudaEventCreate(&b), "cudaEventCreate");
+        pev.push_back(b);
+        ck(cudaEventRecord(a, st_), "cudaEventRecord");
+      }
+      double bytes = 0.0;
+      for (int n = 1; n < n_c_; ++n) {
+        const int mode = (n == 1) ? rp::MODE_FIRST : (n == n_c_ - 1 ? rp::MODE_LAST : rp::MODE_MID);
+        launched(rp::launch_step<T>(H_, d_fdev_, rows_.field, rows_.win, k, R, phi[(n - 1) % 3],
+                                    n >= 2 ? phi[(n - 2) % 3] : nullptr,
+                                    mode == rp::MODE_LAST ? nullptr : phi[n % 3], Q, X_, d_coef_,
+                                    n_c_, n, mode, st_),
+                 "step kernel");
+        step_launches++;
+        bytes += (mode == rp::MODE_FIRST ? 3.5 : (mode == rp::MODE_MID ? 5.25 : 4.25)) * vbytes * (double)act;
+      }
+      if (o_.profile) {
+        ck(cudaEventRecord(pev.back(), st_), "cudaEventRecord");
+        pev_bytes.push_back(bytes);
+        pev_launches.push_back(n_c_ - 1);
+      }
+      step_bytes_all += bytes;
+      row_terms += act * (long long)n_c_;
+      launched(rp::launch_gram_integrate<T>(X_, d_W_, rows_.field, rows_.win, k, R, hs_.Z, n_c_,
+                                            rows_.integral, st_),
+               "gram-integral kernel");
+      // rows whose window ends after this macro-step: finish and refill
+      bool any = false;
+      for (int r = 0; r < R; ++r) {
+        h_flag[r] = (h_win[r].y == k + 1 && h_win[r].x <= k) ? 1 : 0;
+        any = any || h_flag[r];
+      }
+      if (!any) continue;
+      ck(cudaMemcpyAsync(rows_.flag, h_flag.data(), R * sizeof(int), cudaMemcpyHostToDevice, st_), "h2d flags");
+      h2d += (long long)R * sizeof(int);
+      launched(rp::launch_norm<T>(S0_, S1_, rows_.win, rows_.flag, R, hs_.Z, rows_.survival, st_), "norm kernel");
+      launched(rp::launch_finalize(rows_, R, hs_.k_S, d_ps, st_), "finalize kernel");
+      bool refill = false;
+      for (int r = 0; r < R; ++r) {
+        if (!h_flag[r]) continue;
+        if (next < n_items) {
+          assign(r, k + 1);
+          refill = true;
+        } else {
+          h_flag[r] = 0;
+          --live;
+        }
+      }
+      if (refill) {
+        upload_rows();
+        init_flagged();
+      }
+    }
+  }
+
+  void set_seed(uint64_t seed) { seed_ = seed; }
+
+ private:
+  void launched(cudaError_t e, const char* what) {
+    ck(e, what);
+    launches++;
+  }
+  const rp::HostSystem& hs_;
+  const rp_options& o_;
+  int n_c_;
+  cudaStream_t st_;
+  Arena& ar_;
+  rp::HamDev<T> H_;
+  rp::LayoutDev L_;
+  uint64_t seed_ = 0;
+  int R_ = 0;
+  rp::FieldDev<T>* d_fdev_ = nullptr;
+  T* d_coef_ = nullptr;
+  double* d_W_ = nullptr;
+  T *S0_ = nullptr, *S1_ = nullptr, *F1_ = nullptr, *F2_ = nullptr, *X_ = nullptr;
+  double* amps_ = nullptr;
+  rp::RowsDev rows_{};
+};
+
+// Rows to allocate: the caller's cap, else 45 % of free device memory.
+template <typename T>
+int choose_rows(const rp::HostSystem& hs, const rp_options& o, int n_c, long long items) {
+  long long cap = o.max_rows > 0 ? o.max_rows : 0;
+  if (cap == 0) {
+    size_t fr = 0, tot = 0;
+    ck(cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
+    cap = std::max<long long>(1, (long long)(0.45 * (double)fr / (double)YieldEngine<T>::row_bytes(hs.Z, n_c)));
+  }
+  cap = std::min<long long>(cap, 65535);
+  return (int)std::max<long long>(1, std::min<long long>(items, cap));
 }
+
+std::vector<Item> make_items(const std::vector<rp::FieldPlan>& plans, const std::vector<long long>& first,
+                             const std::vector<long long>& count, const std::vector<long long>& out0,
+                             long long sample_offset, bool deterministic) {
+  // most expensive fields first, so that rows finish in waves
+  std::vector<int> forder(plans.size());
+  for (size_t f = 0; f < plans.size(); ++f) forder[f] = (int)f;
+  std::stable_sort(forder.begin(), forder.end(),
+                   [&](int a, int b) { return plans[a].n_macro > plans[b].n_macro; });
+  std::vector<Item> items;
+  for (int f : forder)
+    for (long long s = first[f]; s < first[f] + count[f]; ++s)
+      items.push_back(Item{f, deterministic ? s : sample_offset + s, out0[f] + (s - first[f]),
+                           (int)plans[f].n_macro});
+  return items;
+}
+
+rp_status plan_all(const rp::HostSystem& hs, int n_fields, const double* fields, double t_max,
+                   int n_c, double tol, std::vector<rp::FieldPlan>& plans) {
+  plans.resize(n_fields);
+  for (int f = 0; f < n_fields; ++f) {
+    std::string e = rp::plan_field(hs, fields[f], t_max, n_c, tol, true, &plans[f]);
+    if (!e.empty()) return fail(RP_ENOTCONV, "field " + std::to_string(f) + ": " + e);
+    if (plans[f].n_macro > 2000000000LL) return fail(RP_ENOTCONV, "too many macro-steps");
+  }
+  return RP_OK;
+}
+
+template <typename T>
+void fill_stats(rp_stats* stats, const YieldEngine<T>& eng, long long items, int R, int n_c,
+                cudaEvent_t ev0, cudaEvent_t ev1, bool profile, long long d2h) {
+  if (!stats) return;
+  std::memset(stats, 0, sizeof(*stats));
+  stats->kernel_launches = eng.launches;
+  stats->step_launches = eng.step_launches;
+  stats->row_terms = eng.row_terms;
+  stats->propagations = items;
+  stats->rows = R;
+  stats->n_cheb = n_c;
+  float ms = 0.f;
+  ck(cudaEventElapsedTime(&ms, ev0, ev1), "cudaEventElapsedTime");
+  stats->device_ms = ms;
+  double pms = 0.0, pb = 0.0;
+  long long pl = 0;
+  for (size_t i = 0; i + 1 < eng.pev.size(); i += 2) {
+    float t = 0.f;
+    ck(cudaEventElapsedTime(&t, eng.pev[i], eng.pev[i + 1]), "cudaEventElapsedTime");
+    pms += t;
+    pb += eng.pev_bytes[i / 2];
+    pl += eng.pev_launches[i / 2];
+  }
+  stats->step_ms = pms;
+  stats->step_bytes = profile ? pb : eng.step_bytes_all;
+  stats->step_launches_timed = pl;
+  stats->h2d_bytes = eng.h2d;
+  stats->d2h_bytes = d2h;
+}
+
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  EventPair() {
+    ck(cudaEventCreate(&a), "cudaEventCreate");
+    ck(cudaEventCreate(&b), "cudaEventCreate");
+  }
+  ~EventPair() {
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+  }
+};
 
 template <typename T>
 rp_status run_yields(rp_system* sys, int n_fields, const double* fields, int M, uint64_t seed,
@@ -177,220 +458,151 @@ rp_status run_yields(rp_system* sys, int n_fields, const double* fields, int M, 
   if (n_c % 4 != 0 || n_c < 8 || n_c > 88)
     return fail(RP_EINVAL, "n_cheb must be a multiple of 4 in [8, 88]");
   const long long Mr = o.deterministic ? hs.Z : (long long)M;
-  const long long Z = hs.Z;
+  std::vector<rp::FieldPlan> plans;
+  rp_status ps = plan_all(hs, n_fields, fields, t_max, n_c, tol, plans);
+  if (ps != RP_OK) return ps;
+  std::vector<long long> first(n_fields, 0), count(n_fields, Mr), out0(n_fields);
+  for (int f = 0; f < n_fields; ++f) out0[f] = (long long)f * Mr;
+  const std::vector<Item> items = make_items(plans, first, count, out0, o.sample_offset, o.deterministic);
+  const long long n_items = (long long)items.size();
+  const int R = choose_rows<T>(hs, o, n_c, n_items);
 
-  // plans per field
-  std::vector<rp::FieldPlan> plans(n_fields);
-  for (int f = 0; f < n_fields; ++f) {
-    std::string e = rp::plan_field(hs, fields[f], t_max, n_c, tol, true, &plans[f]);
-    if (!e.empty()) return fail(RP_ENOTCONV, "field " + std::to_string(f) + ": " + e);
-  }
-  // work items, most expensive field first
-  std::vector<int> forder(n_fields);
-  for (int f = 0; f < n_fields; ++f) forder[f] = f;
-  std::stable_sort(forder.begin(), forder.end(),
-                   [&](int a, int b) { return plans[a].n_macro > plans[b].n_macro; });
-  const long long items = (long long)n_fields * Mr;
-
-  // rows from the memory budget
-  const size_t vec_elems = (size_t)Z * 8;  // T per state vector
-  const size_t per_row = (4 * vec_elems + (size_t)n_c * Z * 2) * sizeof(T) +
-                         256 + rp::kMaxNucDev * 20 * 8;
-  long long rows_cap = o.max_rows > 0 ? o.max_rows : 0;
-  if (rows_cap == 0) {
-    size_t fr = 0, tot = 0;
-    ck(cudaMemGetInfo(&fr, &tot), "cudaMemGetInfo");
-    const double budget = 0.45 * (double)fr;
-    rows_cap = std::max<long long>(1, (long long)(budget / (double)per_row));
-  }
-  rows_cap = std::min<long long>(rows_cap, 65535);
-  const int R = (int)std::min<long long>(items, rows_cap);
-
-  Counter cnt;
-  cudaEvent_t ev0, ev1;
-  ck(cudaEventCreate(&ev0), "cudaEventCreate");
-  ck(cudaEventCreate(&ev1), "cudaEventCreate");
-  struct EvGuard {
-    cudaEvent_t a, b;
-    ~EvGuard() {
-      cudaEventDestroy(a);
-      cudaEventDestroy(b);
-    }
-  } evg{ev0, ev1};
-  std::vector<cudaEvent_t> pev;  // profiling event pairs
-  struct PevGuard {
-    std::vector<cudaEvent_t>* v;
-    ~PevGuard() {
-      for (auto e : *v) cudaEventDestroy(e);
-    }
-  } pevg{&pev};
-  std::vector<double> pev_bytes;
-  std::vector<long long> pev_launches;
-  ck(cudaEventRecord(ev0, st), "cudaEventRecord");
-
-  long long row_terms = 0;
-  double step_bytes_all = 0.0;
-  long long h2d = 0, d2h = 0;
+  EventPair ev;
+  long long d2h = 0;
   {
     Arena ar(st);
-    T* S0 = ar.get<T>((size_t)R * vec_elems);
-    T* S1 = ar.get<T>((size_t)R * vec_elems);
-    T* F1 = ar.get<T>((size_t)R * vec_elems);
-    T* F2 = ar.get<T>((size_t)R * vec_elems);
-    T* X = ar.get<T>((size_t)R * n_c * Z * 2);
-    double* amps = ar.get<double>((size_t)R * rp::kMaxNucDev * 10 * 2);
-    int* d_field = ar.get<int>(R);
-    int* d_nmacro = ar.get<int>(R);
-    long long* d_sample = ar.get<long long>(R);
-    long long* d_out = ar.get<long long>(R);
-    double* d_int = ar.get<double>(2 * (size_t)R);
-    double* d_surv = d_int + R;
-    double* d_ps = ar.get<double>((size_t)items * 3);
+    YieldEngine<T> eng(hs, o, n_c, st, ar);
+    eng.set_seed(seed);
+    ck(cudaEventRecord(ev.a, st), "cudaEventRecord");
+    eng.set_fields(plans);
+    eng.alloc_rows(R);
+    double* d_ps = ar.get<double>((size_t)n_items * 3);
     double* d_stats = ar.get<double>((size_t)n_fields * 5);
-    rp::FieldDev<T>* d_fdev = ar.get<rp::FieldDev<T>>(n_fields);
-    T* d_coef = ar.get<T>((size_t)n_fields * n_c * 2);
-    double* d_W = ar.get<double>((size_t)n_fields * n_c * n_c * 2);
-
-    // per-field tables
-    std::vector<rp::FieldDev<T>> fdev(n_fields);
-    std::vector<T> coef((size_t)n_fields * n_c * 2);
-    std::vector<double> W((size_t)n_fields * n_c * n_c * 2);
+    long long* d_off = ar.get<long long>(2 * (size_t)n_fields);
+    eng.run(items, d_ps);
+    std::vector<long long> offcnt(2 * (size_t)n_fields);
     for (int f = 0; f < n_fields; ++f) {
-      const rp::FieldPlan& P = plans[f];
-      fdev[f].omega = (T)P.omega;
-      fdev[f].s = (T)(1.0 / P.dE);
-      fdev[f].sh_re = (T)(P.E_c / P.dE);
-      fdev[f].sh_im = (T)0;
-      for (int n = 0; n < n_c; ++n) {
-        coef[((size_t)f * n_c + n) * 2] = (T)P.coef[n].real();
-        coef[((size_t)f * n_c + n) * 2 + 1] = (T)P.coef[n].imag();
-      }
-      for (size_t i = 0; i < (size_t)n_c * n_c; ++i) {
-        W[((size_t)f * n_c * n_c + i) * 2] = P.W[i].real();
-        W[((size_t)f * n_c * n_c + i) * 2 + 1] = P.W[i].imag();
-      }
+      offcnt[f] = out0[f];
+      offcnt[n_fields + f] = Mr;
     }
-    ck(cudaMemcpyAsync(d_fdev, fdev.data(), fdev.size() * sizeof(fdev[0]), cudaMemcpyHostToDevice, st), "h2d fields");
-    ck(cudaMemcpyAsync(d_coef, coef.data(), coef.size() * sizeof(T), cudaMemcpyHostToDevice, st), "h2d coef");
-    ck(cudaMemcpyAsync(d_W, W.data(), W.size() * sizeof(double), cudaMemcpyHostToDevice, st), "h2d W");
-    h2d += (long long)(fdev.size() * sizeof(fdev[0]) + coef.size() * sizeof(T) + W.size() * sizeof(double));
-
-    const rp::HamDev<T> H = make_ham<T>(hs);
-    const rp::LayoutDev L = make_layout(hs);
-    const double vbytes = (double)vec_elems * sizeof(T);  // one state vector
-
-    std::vector<int> h_field(R), h_nmacro(R);
-    std::vector<long long> h_sample(R), h_out(R);
-    for (long long b0 = 0; b0 < items; b0 += R) {
-      const int rows = (int)std::min<long long>(R, items - b0);
-      long long max_macro = 0;
-      std::vector<long long> active_by_macro;
-      for (int r = 0; r < rows; ++r) {
-        const long long it = b0 + r;
-        const int f = forder[it / Mr];
-        const long long s = it % Mr;
-        h_field[r] = f;
-        h_nmacro[r] = (int)plans[f].n_macro;
-        h_sample[r] = o.deterministic ? s : o.sample_offset + s;
-        h_out[r] = (long long)f * Mr + s;
-        max_macro = std::max<long long>(max_macro, plans[f].n_macro);
-      }
-      active_by_macro.assign(max_macro, 0);
-      for (int r = 0; r < rows; ++r)
-        for (long long k = 0; k < h_nmacro[r]; ++k) active_by_macro[k]++;
-      ck(cudaMemcpyAsync(d_field, h_field.data(), rows * sizeof(int), cudaMemcpyHostToDevice, st), "h2d");
-      ck(cudaMemcpyAsync(d_nmacro, h_nmacro.data(), rows * sizeof(int), cudaMemcpyHostToDevice, st), "h2d");
-      ck(cudaMemcpyAsync(d_sample, h_sample.data(), rows * sizeof(long long), cudaMemcpyHostToDevice, st), "h2d");
-      ck(cudaMemcpyAsync(d_out, h_out.data(), rows * sizeof(long long), cudaMemcpyHostToDevice, st), "h2d");
-      h2d += (long long)rows * (2 * sizeof(int) + 2 * sizeof(long long));
-      launched(cnt, rp::launch_zero(d_int, 2 * (size_t)R, st), "zero integrals");
-      if (!o.deterministic)
-        launched(cnt, rp::launch_coherent_amps(L, d_sample, rows, seed, o.pair_id, amps, nullptr, st),
-                 "coherent amplitudes");
-      launched(cnt, rp::launch_init_state<T>(L, amps, d_sample, rows, o.deterministic, S0, st),
-               "initial states");
-
-      T* Sb[2] = {S0, S1};
-      for (long long k = 0; k < max_macro; ++k) {
-        T* P = Sb[k & 1];
-        T* Q = Sb[(k + 1) & 1];
-        T* phi[3] = {P, F1, F2};
-        const long long act = active_by_macro[k];
-        const bool prof = o.profile != 0;
-        if (prof) {
-          cudaEvent_t a, b;
-          ck(cudaEventCreate(&a), "cudaEventCreate");
-          pev.push_back(a);
-          ck(cudaEventCreate(&b), "cudaEventCreate");
-          pev.push_back(b);
-          ck(cudaEventRecord(a, st), "cudaEventRecord");
-        }
-        double bytes = 0.0;
-        for (int n = 1; n < n_c; ++n) {
-          const int mode = (n == 1) ? rp::MODE_FIRST : (n == n_c - 1 ? rp::MODE_LAST : rp::MODE_MID);
-          const T* cur = phi[(n - 1) % 3];
-          const T* prv = n >= 2 ? phi[(n - 2) % 3] : nullptr;
-          T* nxt = phi[n % 3];
-          launched(cnt, rp::launch_step<T>(H, d_fdev, d_field, d_nmacro, k, rows, cur, prv,
-                                           mode == rp::MODE_LAST ? nullptr : nxt, Q, X, d_coef,
-                                           n_c, n, mode, st),
-                   "step kernel");
-          cnt.step_launches++;
-          const double vmul = mode == rp::MODE_FIRST ? 3.5 : (mode == rp::MODE_MID ? 5.25 : 4.25);
-          bytes += vmul * vbytes * (double)act;
-        }
-        if (prof) {
-          ck(cudaEventRecord(pev.back(), st), "cudaEventRecord");
-          pev_bytes.push_back(bytes);
-          pev_launches.push_back(n_c - 1);
-        }
-        step_bytes_all += bytes;
-        row_terms += act * (long long)n_c;
-        launched(cnt, rp::launch_gram_integrate<T>(X, d_W, d_field, d_nmacro, k, rows, Z, n_c,
-                                                   d_int, st),
-                 "gram-integral kernel");
-      }
-      launched(cnt, rp::launch_norm<T>(S0, S1, d_nmacro, rows, Z, d_surv, st), "norm kernel");
-      rp::RowsDev RD{d_field, d_nmacro, d_sample, d_out, d_int, d_surv};
-      launched(cnt, rp::launch_finalize(RD, rows, hs.k_S, d_ps, st), "finalize kernel");
-    }
-    launched(cnt, rp::launch_stats(d_ps, n_fields, Mr, d_stats, st), "stats kernel");
+    ck(cudaMemcpyAsync(d_off, offcnt.data(), offcnt.size() * sizeof(long long), cudaMemcpyHostToDevice, st), "h2d");
+    eng.h2d += (long long)(offcnt.size() * sizeof(long long));
+    ck(rp::launch_stats(d_ps, d_off, d_off + n_fields, n_fields, d_stats, st), "stats kernel");
+    eng.launches++;
     ck(cudaMemcpyAsync(out, d_stats, (size_t)n_fields * 5 * sizeof(double), cudaMemcpyDeviceToHost, st), "d2h stats");
     d2h += (long long)n_fields * 5 * sizeof(double);
     if (per_sample) {
-      ck(cudaMemcpyAsync(per_sample, d_ps, (size_t)items * 3 * sizeof(double), cudaMemcpyDeviceToHost, st), "d2h per-sample");
-      d2h += (long long)items * 3 * sizeof(double);
+      ck(cudaMemcpyAsync(per_sample, d_ps, (size_t)n_items * 3 * sizeof(double), cudaMemcpyDeviceToHost, st), "d2h per-sample");
+      d2h += (long long)n_items * 3 * sizeof(double);
     }
-    ck(cudaEventRecord(ev1, st), "cudaEventRecord");
+    ck(cudaEventRecord(ev.b, st), "cudaEventRecord");
     ck(cudaStreamSynchronize(st), "kernel execution");
+    fill_stats(stats, eng, n_items, R, n_c, ev.a, ev.b, o.profile != 0, d2h);
   }
   ck(cudaStreamSynchronize(st), "free");
-  if (stats) {
-    std::memset(stats, 0, sizeof(*stats));
-    stats->kernel_launches = cnt.launches;
-    stats->step_launches = cnt.step_launches;
-    stats->row_terms = row_terms;
-    stats->propagations = items;
-    stats->rows = R;
-    stats->n_cheb = n_c;
-    float ms = 0.f;
-    ck(cudaEventElapsedTime(&ms, ev0, ev1), "cudaEventElapsedTime");
-    stats->device_ms = ms;
-    double pms = 0.0, pb = 0.0;
-    long long pl = 0;
-    for (size_t i = 0; i + 1 < pev.size(); i += 2) {
-      float t = 0.f;
-      ck(cudaEventElapsedTime(&t, pev[i], pev[i + 1]), "cudaEventElapsedTime");
-      pms += t;
-      pb += pev_bytes[i / 2];
-      pl += pev_launches[i / 2];
+  return RP_OK;
+}
+
+// Rounds of samples per field until each field's standard error (Eq. 23)
+// reaches se_target: M_min samples everywhere first, then per field the
+// samples its measured spread asks for, (sigma_f / se_target)^2 with a 15 %
+// margin, capped at M_max.  Sample s is the same direction set at every field.
+template <typename T>
+rp_status run_converged(rp_system* sys, int n_fields, const double* fields, double se_target,
+                        int M_min, int M_max, uint64_t seed, double t_max, const rp_options& o,
+                        double* out, int* M_used, rp_stats* stats) {
+  const rp::HostSystem& hs = sys->hs;
+  cudaStream_t st = (cudaStream_t)o.stream;
+  const int n_c = o.n_cheb > 0 ? o.n_cheb : default_ncheb(o.precision);
+  const double tol = o.tol > 0 ? o.tol : default_tol(o.precision);
+  if (n_c % 4 != 0 || n_c < 8 || n_c > 88)
+    return fail(RP_EINVAL, "n_cheb must be a multiple of 4 in [8, 88]");
+  std::vector<rp::FieldPlan> plans;
+  rp_status ps = plan_all(hs, n_fields, fields, t_max, n_c, tol, plans);
+  if (ps != RP_OK) return ps;
+  std::vector<std::vector<double>> samp(n_fields);  // phi_S, phi_T, survival triples
+  std::vector<long long> have(n_fields, 0), want(n_fields, M_min);
+  EventPair ev;
+  long long d2h = 0, total_items = 0;
+  int R = 0;
+  {
+    Arena ar(st);
+    YieldEngine<T> eng(hs, o, n_c, st, ar);
+    eng.set_seed(seed);
+    ck(cudaEventRecord(ev.a, st), "cudaEventRecord");
+    eng.set_fields(plans);
+    R = choose_rows<T>(hs, o, n_c, std::max<long long>((long long)n_fields * M_min, 256));
+    eng.alloc_rows(R);
+    for (int round = 0; round < 8; ++round) {
+      std::vector<long long> first(n_fields), count(n_fields), out0(n_fields);
+      long long n = 0;
+      for (int f = 0; f < n_fields; ++f) {
+        first[f] = have[f];
+        count[f] = std::max<long long>(0, want[f] - have[f]);
+        out0[f] = n;
+        n += count[f];
+      }
+      if (n == 0) break;
+      const std::vector<Item> items = make_items(plans, first, count, out0, o.sample_offset, false);
+      double* d_ps = ar.get<double>((size_t)n * 3);
+      eng.run(items, d_ps);
+      std::vector<double> h((size_t)n * 3);
+      ck(cudaMemcpyAsync(h.data(), d_ps, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "d2h round");
+      ck(cudaStreamSynchronize(st), "round");
+      d2h += (long long)h.size() * sizeof(double);
+      total_items += n;
+      for (int f = 0; f < n_fields; ++f) {
+        samp[f].insert(samp[f].end(), h.begin() + out0[f] * 3, h.begin() + (out0[f] + count[f]) * 3);
+        have[f] += count[f];
+      }
+      // next targets from the spread measured so far
+      bool more = false;
+      for (int f = 0; f < n_fields; ++f) {
+        const long long m = have[f];
+        double mean = 0.0, var = 0.0;
+        for (long long i = 0; i < m; ++i) mean += samp[f][3 * i];
+        mean /= (double)m;
+        for (long long i = 0; i < m; ++i) var += (samp[f][3 * i] - mean) * (samp[f][3 * i] - mean);
+        var /= (double)std::max<long long>(m - 1, 1);
+        const double se = std::sqrt(var / (double)m);
+        if (se <= se_target || m >= M_max) {
+          want[f] = m;
+          continue;
+        }
+        const long long need = (long long)std::ceil(1.15 * var / (se_target * se_target)) + 1;
+        want[f] = std::min<long long>(M_max, std::max<long long>(need, m + 1));
+        more = true;
+      }
+      if (!more) break;
     }
-    stats->step_ms = pms;
-    stats->step_bytes = o.profile ? pb : step_bytes_all;
-    stats->step_launches_timed = pl;
-    stats->h2d_bytes = h2d;
-    stats->d2h_bytes = d2h;
+    // final per-field statistics on the device over all rounds' samples
+    long long tot = 0;
+    std::vector<long long> offcnt(2 * (size_t)n_fields);
+    for (int f = 0; f < n_fields; ++f) {
+      offcnt[f] = tot;
+      offcnt[n_fields + f] = have[f];
+      tot += have[f];
+    }
+    std::vector<double> all;
+    all.reserve((size_t)tot * 3);
+    for (int f = 0; f < n_fields; ++f) all.insert(all.end(), samp[f].begin(), samp[f].end());
+    double* d_all = ar.get<double>((size_t)std::max<long long>(tot, 1) * 3);
+    long long* d_off = ar.get<long long>(2 * (size_t)n_fields);
+    double* d_stats = ar.get<double>((size_t)n_fields * 5);
+    ck(cudaMemcpyAsync(d_all, all.data(), all.size() * sizeof(double), cudaMemcpyHostToDevice, st), "h2d");
+    ck(cudaMemcpyAsync(d_off, offcnt.data(), offcnt.size() * sizeof(long long), cudaMemcpyHostToDevice, st), "h2d");
+    eng.h2d += (long long)(all.size() * sizeof(double) + offcnt.size() * sizeof(long long));
+    ck(rp::launch_stats(d_all, d_off, d_off + n_fields, n_fields, d_stats, st), "stats kernel");
+    eng.launches++;
+    ck(cudaMemcpyAsync(out, d_stats, (size_t)n_fields * 5 * sizeof(double), cudaMemcpyDeviceToHost, st), "d2h stats");
+    d2h += (long long)n_fields * 5 * sizeof(double);
+    ck(cudaEventRecord(ev.b, st), "cudaEventRecord");
+    ck(cudaStreamSynchronize(st), "kernel execution");
+    if (M_used)
+      for (int f = 0; f < n_fields; ++f) M_used[f] = (int)have[f];
+    fill_stats(stats, eng, total_items, R, n_c, ev.a, ev.b, o.profile != 0, d2h);
   }
+  ck(cudaStreamSynchronize(st), "free");
   return RP_OK;
 }
 
@@ -562,6 +774,41 @@ rp_status rp_yields(rp_system* s, int n_fields, const double* fields, int M, uin
   }
 }
 
+rp_status rp_yields_converged(rp_system* s, int n_fields, const double* fields, double se_target,
+                              int M_min, int M_max, uint64_t seed, double t_max,
+                              const rp_options* opt, double* out, int* M_used, rp_stats* stats) {
+  g_err.clear();
+  rp_options o;
+  if (opt) o = *opt;
+  else rp_default_options(&o);
+  if (!s) return fail(RP_EINVAL, "system is NULL");
+  if (n_fields < 0) return fail(RP_EINVAL, "n_fields must be >= 0");
+  if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
+  if (o.deterministic) return fail(RP_EINVAL, "rp_yields_converged samples coherent states only");
+  if (!(se_target > 0.0) || !std::isfinite(se_target)) return fail(RP_EINVAL, "se_target must be positive");
+  if (M_min < 2 || M_max < M_min) return fail(RP_EINVAL, "need 2 <= M_min <= M_max");
+  if (!(t_max > 0.0) || !std::isfinite(t_max)) return fail(RP_EINVAL, "t_max must be positive and finite");
+  if (o.sample_offset < 0) return fail(RP_EINVAL, "sample_offset must be >= 0");
+  if (n_fields > 0 && (!fields || !out)) return fail(RP_EINVAL, "NULL fields or out");
+  for (int f = 0; f < n_fields; ++f)
+    if (!std::isfinite(fields[f])) return fail(RP_EINVAL, "non-finite field");
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  if (n_fields == 0) return RP_OK;
+  rp_status ds = check_device();
+  if (ds != RP_OK) return ds;
+  try {
+    if (o.precision == RP_FP64)
+      return run_converged<double>(s, n_fields, fields, se_target, M_min, M_max, seed, t_max, o,
+                                   out, M_used, stats);
+    return run_converged<float>(s, n_fields, fields, se_target, M_min, M_max, seed, t_max, o, out,
+                                M_used, stats);
+  } catch (const CudaFail& e) {
+    return fail(e.st, e.msg);
+  } catch (const std::bad_alloc&) {
+    return fail(RP_ENOMEM, "host allocation failed");
+  }
+}
+
 rp_status rp_apply_h(rp_system* s, double B, int precision, int n_vec, const void* x, void* y,
                      void* stream) {
   g_err.clear();
@@ -622,11 +869,13 @@ rp_status rp_init_states(rp_system* s, int precision, uint64_t seed, uint32_t pa
     double* uv = angles ? ar.get<double>((size_t)n * std::max(hs.n_nuc, 1) * 2) : nullptr;
     ck(cudaMemcpyAsync(d_s, smp.data(), n * sizeof(long long), cudaMemcpyHostToDevice, st), "h2d");
     const rp::LayoutDev L = make_layout(hs);
-    ck(rp::launch_coherent_amps(L, d_s, n, seed, pair_id, amps, uv, st), "coherent amplitudes");
+    ck(rp::launch_coherent_amps(L, d_s, nullptr, n, seed, pair_id, amps, uv, st), "coherent amplitudes");
     if (precision == RP_FP64)
-      ck(rp::launch_init_state<double>(L, amps, d_s, n, 0, (double*)psi, st), "initial states");
+      ck(rp::launch_init_state<double>(L, amps, d_s, nullptr, nullptr, n, 0, (double*)psi,
+                                       (double*)psi, nullptr, nullptr, st), "initial states");
     else
-      ck(rp::launch_init_state<float>(L, amps, d_s, n, 0, (float*)psi, st), "initial states");
+      ck(rp::launch_init_state<float>(L, amps, d_s, nullptr, nullptr, n, 0, (float*)psi,
+                                      (float*)psi, nullptr, nullptr, st), "initial states");
     if (angles && hs.n_nuc > 0)
       ck(cudaMemcpyAsync(angles, uv, (size_t)n * hs.n_nuc * 2 * sizeof(double), cudaMemcpyDeviceToHost, st), "d2h");
     ck(cudaStreamSynchronize(st), "init kernels");

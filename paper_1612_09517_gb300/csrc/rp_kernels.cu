@@ -255,7 +255,7 @@ __device__ __forceinline__ void half_nucleus(Cx<T> (&y)[4], T (&b1)[3], T (&b2)[
 template <typename T, bool ANISO>
 __global__ void __launch_bounds__(kStepThreads, sizeof(T) == 4 ? 4 : 2) k_cheb_step(
     const HamDev<T> H, const FieldDev<T>* __restrict__ fields, const int* __restrict__ row_field,
-    const int* __restrict__ row_nmacro, long long macro, const T* __restrict__ cur,
+    const int2* __restrict__ row_win, int macro, const T* __restrict__ cur,
     const T* __restrict__ prev, T* __restrict__ next, T* __restrict__ acc, T* __restrict__ X,
     const T* __restrict__ coef, int n_c, int n, int mode, int n_in) {
   extern __shared__ __align__(16) unsigned char step_smem[];
@@ -265,7 +265,8 @@ __global__ void __launch_bounds__(kStepThreads, sizeof(T) == 4 ? 4 : 2) k_cheb_s
   const int r = blockIdx.y;
   int f = 0;
   if (mode != MODE_APPLY) {
-    if (macro >= row_nmacro[r]) return;  // the whole block: one row
+    const int2 w = row_win[r];
+    if (macro < w.x || macro >= w.y) return;  // the whole block: one row
     f = row_field[r];
   }
   const bool valid = m < Z;
@@ -452,10 +453,13 @@ constexpr int kGramThreads = 256;
 template <typename T>
 __global__ void __launch_bounds__(kGramThreads) k_gram_integrate(
     const T* __restrict__ X, const double* __restrict__ W, const int* __restrict__ row_field,
-    const int* __restrict__ row_nmacro, long long macro, long long Z, int n_c, int tiles,
+    const int2* __restrict__ row_win, int macro, long long Z, int n_c, int tiles,
     int groups, int zc, long long z_per_cta, double* __restrict__ integral) {
   const int r = blockIdx.y;
-  if (macro >= row_nmacro[r]) return;
+  {
+    const int2 w = row_win[r];
+    if (macro < w.x || macro >= w.y) return;
+  }
   const long long z0 = (long long)blockIdx.x * z_per_cta;
   const long long z1 = min(Z, z0 + z_per_cta);
   if (z0 >= z1) return;
@@ -567,14 +571,17 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_integrate(
   if (tid == 0) atomicAdd(integral + r, tot);
 }
 
-// survival[r] += |psi|^2 over a slice; psi of row r sits in S[n_macro % 2].
+// survival[r] += |psi|^2 over a slice for the flagged rows; psi of a row whose
+// window ended at macro-step e sits in S[e % 2].
 template <typename T>
 __global__ void __launch_bounds__(256) k_norm(const T* __restrict__ S0, const T* __restrict__ S1,
-                                              const int* __restrict__ row_nmacro, long long Z,
+                                              const int2* __restrict__ row_win,
+                                              const int* __restrict__ row_flag, long long Z,
                                               long long z_per_cta, double* __restrict__ survival) {
   __shared__ double sh[256];
   const int r = blockIdx.y;
-  const T* S = ((row_nmacro[r] & 1) ? S1 : S0) + (size_t)r * Z * 8;
+  if (row_flag && !row_flag[r]) return;
+  const T* S = ((row_win[r].y & 1) ? S1 : S0) + (size_t)r * Z * 8;
   const long long z0 = (long long)blockIdx.x * z_per_cta;
   const long long z1 = min(Z, z0 + z_per_cta);
   double s = 0.0;
@@ -591,7 +598,7 @@ __global__ void __launch_bounds__(256) k_norm(const T* __restrict__ S0, const T*
 
 __global__ void k_finalize(RowsDev R, int rows, double k_S, double* __restrict__ per_sample) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= rows) return;
+  if (r >= rows || (R.flag && !R.flag[r])) return;
   const double phiS = k_S * R.integral[r];
   const double surv = R.survival[r];
   double* o = per_sample + (size_t)R.out[r] * 3;
@@ -601,23 +608,28 @@ __global__ void k_finalize(RowsDev R, int rows, double k_S, double* __restrict__
 }
 
 // Per field: mean of phi_S, phi_T (Eq. 18) and their standard errors
-// sigma/sqrt(M) with the M-1 sample variance (Eq. 23), and mean survival.
-__global__ void __launch_bounds__(256) k_stats(const double* __restrict__ per_sample, long long M,
+// sigma/sqrt(M) with the M-1 sample variance (Eq. 23), and mean survival, over
+// the samples per_sample[off[f] .. off[f] + cnt[f]).
+__global__ void __launch_bounds__(256) k_stats(const double* __restrict__ per_sample,
+                                               const long long* __restrict__ off,
+                                               const long long* __restrict__ cnt,
                                                double* __restrict__ out) {
   __shared__ double sh[256];
   const int f = blockIdx.x;
-  const double* p = per_sample + (size_t)f * M * 3;
+  const double* p = per_sample + (size_t)off[f] * 3;
+  const long long M = cnt[f];
   double s0 = 0, s1 = 0, s2 = 0;
   for (long long i = threadIdx.x; i < M; i += blockDim.x) {
     s0 += p[3 * i];
     s1 += p[3 * i + 1];
     s2 += p[3 * i + 2];
   }
-  const double m0 = block_sum<256>(s0, sh) / (double)M;
+  const double Md = M > 0 ? (double)M : 1.0;
+  const double m0 = block_sum<256>(s0, sh) / Md;
   __syncthreads();
-  const double m1 = block_sum<256>(s1, sh) / (double)M;
+  const double m1 = block_sum<256>(s1, sh) / Md;
   __syncthreads();
-  const double m2 = block_sum<256>(s2, sh) / (double)M;
+  const double m2 = block_sum<256>(s2, sh) / Md;
   __syncthreads();
   double v0 = 0, v1 = 0;
   for (long long i = threadIdx.x; i < M; i += blockDim.x) {
@@ -632,8 +644,8 @@ __global__ void __launch_bounds__(256) k_stats(const double* __restrict__ per_sa
     const double den = (M > 1) ? (double)(M - 1) : 1.0;
     out[5 * f + 0] = m0;
     out[5 * f + 1] = m1;
-    out[5 * f + 2] = sqrt(q0 / den / (double)M);
-    out[5 * f + 3] = sqrt(q1 / den / (double)M);
+    out[5 * f + 2] = sqrt(q0 / den / Md);
+    out[5 * f + 3] = sqrt(q1 / den / Md);
     out[5 * f + 4] = m2;
   }
 }
@@ -668,11 +680,12 @@ __device__ __forceinline__ double u53(uint32_t hi, uint32_t lo) {
 // coherent-state components c_j = sqrt(C(2I, j)) cos^{2I-j}(theta/2)
 // sin^j(theta/2) e^{i j phi}, j = I - M (Eq. 15 expanded in |I, M>).
 __global__ void k_coherent_amps(const LayoutDev L, const long long* __restrict__ row_sample,
-                                int rows, uint64_t seed, uint32_t pair, double* __restrict__ amps,
-                                double* __restrict__ uv) {
+                                const int* __restrict__ row_flag, int rows, uint64_t seed,
+                                uint32_t pair, double* __restrict__ amps, double* __restrict__ uv) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= rows * L.n_nuc) return;
   const int r = t / L.n_nuc, p = t % L.n_nuc;
+  if (row_flag && !row_flag[r]) return;
   const int k = L.input_index[p];
   const unsigned long long s = (unsigned long long)row_sample[r];
   uint32_t c[4] = {(uint32_t)k, (uint32_t)(s & 0xFFFFFFFFull), (uint32_t)(s >> 32), pair};
@@ -699,14 +712,26 @@ __global__ void k_coherent_amps(const LayoutDev L, const long long* __restrict__
 }
 
 // psi(m, e) = <e|S> prod_p c_p(j_p)  (Eq. 19), or the basis state |S, m0> (Eq. 13).
+// Flagged rows only (all rows when row_flag is NULL); the state goes to
+// S[start % 2] of the row's window, and the row's integral and survival restart.
 template <typename T>
 __global__ void __launch_bounds__(256) k_init_state(const LayoutDev L,
                                                     const double* __restrict__ amps,
                                                     const long long* __restrict__ row_sample,
-                                                    int deterministic, T* __restrict__ psi) {
+                                                    const int* __restrict__ row_flag,
+                                                    const int2* __restrict__ row_win,
+                                                    int deterministic, T* __restrict__ S0,
+                                                    T* __restrict__ S1, double* __restrict__ integral,
+                                                    double* __restrict__ survival) {
   const long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
+  if (row_flag && !row_flag[r]) return;
+  if (m == 0 && integral) {
+    integral[r] = 0.0;
+    survival[r] = 0.0;
+  }
   if (m >= L.Z) return;
+  T* psi = (row_win && (row_win[r].x & 1)) ? S1 : S0;
   double pr = 1.0, pi = 0.0;
   if (deterministic) {
     pr = (m == row_sample[r]) ? 1.0 : 0.0;
@@ -741,30 +766,34 @@ inline unsigned grid1(long long n, int b) { return (unsigned)((n + b - 1) / b); 
 
 }  // namespace
 
-cudaError_t launch_coherent_amps(const LayoutDev& L, const long long* row_sample, int rows,
-                                 uint64_t seed, uint32_t pair, double* amps, double* uv,
-                                 cudaStream_t st) {
+cudaError_t launch_coherent_amps(const LayoutDev& L, const long long* row_sample,
+                                 const int* row_flag, int rows, uint64_t seed, uint32_t pair,
+                                 double* amps, double* uv, cudaStream_t st) {
   const long long n = (long long)rows * L.n_nuc;
   if (n == 0) return cudaSuccess;
-  k_coherent_amps<<<grid1(n, 128), 128, 0, st>>>(L, row_sample, rows, seed, pair, amps, uv);
+  k_coherent_amps<<<grid1(n, 128), 128, 0, st>>>(L, row_sample, row_flag, rows, seed, pair, amps,
+                                                 uv);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_init_state(const LayoutDev& L, const double* amps, const long long* row_sample,
-                              int rows, int deterministic, T* psi, cudaStream_t st) {
+                              const int* row_flag, const int2* row_win, int rows,
+                              int deterministic, T* S0, T* S1, double* integral, double* survival,
+                              cudaStream_t st) {
   if (rows == 0) return cudaSuccess;
   const int b = L.Z >= 256 ? 256 : (int)((L.Z + 31) / 32 * 32);
   dim3 grid(grid1(L.Z, b), rows);
-  k_init_state<T><<<grid, b, 0, st>>>(L, amps, row_sample, deterministic, psi);
+  k_init_state<T><<<grid, b, 0, st>>>(L, amps, row_sample, row_flag, row_win, deterministic, S0,
+                                      S1, integral, survival);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_step(const HamDev<T>& H, const FieldDev<T>* fields, const int* row_field,
-                        const int* row_nmacro, long long macro, int rows, const T* cur,
-                        const T* prev, T* next, T* acc, T* X, const T* coef, int n_c, int n,
-                        int mode, cudaStream_t st) {
+                        const int2* row_win, int macro, int rows, const T* cur, const T* prev,
+                        T* next, T* acc, T* X, const T* coef, int n_c, int n, int mode,
+                        cudaStream_t st) {
   if (rows == 0) return cudaSuccess;
   // power-of-two blocks so that m XOR 2^p stays inside the block for 2^p < b
   int b = 32;
@@ -775,18 +804,18 @@ cudaError_t launch_step(const HamDev<T>& H, const FieldDev<T>* fields, const int
   const size_t smem = (size_t)b * 4 * sizeof(Cx<T>);
   dim3 grid(grid1(H.Z, b), rows);
   if (H.aniso)
-    k_cheb_step<T, true><<<grid, b, smem, st>>>(H, fields, row_field, row_nmacro, macro, cur, prev,
+    k_cheb_step<T, true><<<grid, b, smem, st>>>(H, fields, row_field, row_win, macro, cur, prev,
                                                 next, acc, X, coef, n_c, n, mode, n_in);
   else
-    k_cheb_step<T, false><<<grid, b, smem, st>>>(H, fields, row_field, row_nmacro, macro, cur,
-                                                 prev, next, acc, X, coef, n_c, n, mode, n_in);
+    k_cheb_step<T, false><<<grid, b, smem, st>>>(H, fields, row_field, row_win, macro, cur, prev,
+                                                 next, acc, X, coef, n_c, n, mode, n_in);
   return cudaGetLastError();
 }
 
 template <typename T>
 cudaError_t launch_gram_integrate(const T* X, const double* W, const int* row_field,
-                                  const int* row_nmacro, long long macro, int rows, long long Z,
-                                  int n_c, double* integral, cudaStream_t st) {
+                                  const int2* row_win, int macro, int rows, long long Z, int n_c,
+                                  double* integral, cudaStream_t st) {
   if (rows == 0) return cudaSuccess;
   const int nt = n_c / 4;
   const int tiles = nt * (nt + 1) / 2;
@@ -803,18 +832,18 @@ cudaError_t launch_gram_integrate(const T* X, const double* W, const int* row_fi
     if (e != cudaSuccess) return e;
   }
   dim3 grid((unsigned)((Z + z_per_cta - 1) / z_per_cta), rows);
-  k_gram_integrate<T><<<grid, kGramThreads, smem, st>>>(X, W, row_field, row_nmacro, macro, Z, n_c,
+  k_gram_integrate<T><<<grid, kGramThreads, smem, st>>>(X, W, row_field, row_win, macro, Z, n_c,
                                                         tiles, groups, zc, z_per_cta, integral);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_norm(const T* S0, const T* S1, const int* row_nmacro, int rows, long long Z,
-                        double* survival, cudaStream_t st) {
+cudaError_t launch_norm(const T* S0, const T* S1, const int2* row_win, const int* row_flag,
+                        int rows, long long Z, double* survival, cudaStream_t st) {
   if (rows == 0) return cudaSuccess;
   long long zper = 256 * 16;
   dim3 grid(grid1(Z, (int)zper), rows);
-  k_norm<T><<<grid, 256, 0, st>>>(S0, S1, row_nmacro, Z, zper, survival);
+  k_norm<T><<<grid, 256, 0, st>>>(S0, S1, row_win, row_flag, Z, zper, survival);
   return cudaGetLastError();
 }
 
@@ -825,10 +854,10 @@ cudaError_t launch_finalize(const RowsDev& R, int rows, double k_S, double* per_
   return cudaGetLastError();
 }
 
-cudaError_t launch_stats(const double* per_sample, int n_fields, long long M, double* out,
-                         cudaStream_t st) {
+cudaError_t launch_stats(const double* per_sample, const long long* off, const long long* cnt,
+                         int n_fields, double* out, cudaStream_t st) {
   if (n_fields == 0) return cudaSuccess;
-  k_stats<<<n_fields, 256, 0, st>>>(per_sample, M, out);
+  k_stats<<<n_fields, 256, 0, st>>>(per_sample, off, cnt, out);
   return cudaGetLastError();
 }
 
@@ -839,26 +868,27 @@ cudaError_t launch_zero(double* p, size_t n, cudaStream_t st) {
 }
 
 template cudaError_t launch_init_state<float>(const LayoutDev&, const double*, const long long*,
-                                              int, int, float*, cudaStream_t);
+                                              const int*, const int2*, int, int, float*, float*,
+                                              double*, double*, cudaStream_t);
 template cudaError_t launch_init_state<double>(const LayoutDev&, const double*, const long long*,
-                                               int, int, double*, cudaStream_t);
+                                               const int*, const int2*, int, int, double*, double*,
+                                               double*, double*, cudaStream_t);
 template cudaError_t launch_step<float>(const HamDev<float>&, const FieldDev<float>*, const int*,
-                                        const int*, long long, int, const float*, const float*,
-                                        float*, float*, float*, const float*, int, int, int,
-                                        cudaStream_t);
+                                        const int2*, int, int, const float*, const float*, float*,
+                                        float*, float*, const float*, int, int, int, cudaStream_t);
 template cudaError_t launch_step<double>(const HamDev<double>&, const FieldDev<double>*,
-                                         const int*, const int*, long long, int, const double*,
+                                         const int*, const int2*, int, int, const double*,
                                          const double*, double*, double*, double*, const double*,
                                          int, int, int, cudaStream_t);
 template cudaError_t launch_gram_integrate<float>(const float*, const double*, const int*,
-                                                  const int*, long long, int, long long, int,
-                                                  double*, cudaStream_t);
+                                                  const int2*, int, int, long long, int, double*,
+                                                  cudaStream_t);
 template cudaError_t launch_gram_integrate<double>(const double*, const double*, const int*,
-                                                   const int*, long long, int, long long, int,
-                                                   double*, cudaStream_t);
-template cudaError_t launch_norm<float>(const float*, const float*, const int*, int, long long,
-                                        double*, cudaStream_t);
-template cudaError_t launch_norm<double>(const double*, const double*, const int*, int, long long,
-                                         double*, cudaStream_t);
+                                                   const int2*, int, int, long long, int, double*,
+                                                   cudaStream_t);
+template cudaError_t launch_norm<float>(const float*, const float*, const int2*, const int*, int,
+                                        long long, double*, cudaStream_t);
+template cudaError_t launch_norm<double>(const double*, const double*, const int2*, const int*,
+                                         int, long long, double*, cudaStream_t);
 
 }  // namespace rp

@@ -37,12 +37,15 @@ struct FieldDev {
 
 enum StepMode { MODE_APPLY = 0, MODE_FIRST = 1, MODE_MID = 2, MODE_LAST = 3 };
 
-// Per-row (one propagation) metadata, device arrays of length rows.
+// Per-row (one propagation) metadata, device arrays of length rows.  A row is
+// active in the macro-steps start <= k < end of its window; rows are refilled
+// with new work items as their windows end.
 struct RowsDev {
-  int* field;        // field index
-  int* n_macro;      // macro-steps this row needs
+  int* field;        // field index (into the per-field tables)
+  int2* win;         // {start, end} macro-step window
   long long* sample; // sample index (coherent) or basis index (deterministic)
-  long long* out;    // output slot field * M + sample_rel
+  long long* out;    // output slot in the per-sample array
+  int* flag;         // rows selected for init / norm / finalize
   double* integral;  // int |P_S psi|^2 dt accumulated (FP64)
   double* survival;  // |psi(T)|^2
 };
@@ -57,37 +60,42 @@ struct LayoutDev {
 };
 
 // ---- launchers (return cudaGetLastError after the launch) ----
+// row_flag may be NULL (all rows).
 
-cudaError_t launch_coherent_amps(const LayoutDev& L, const long long* row_sample, int rows,
-                                 uint64_t seed, uint32_t pair, double* amps, double* uv,
-                                 cudaStream_t st);
+cudaError_t launch_coherent_amps(const LayoutDev& L, const long long* row_sample,
+                                 const int* row_flag, int rows, uint64_t seed, uint32_t pair,
+                                 double* amps, double* uv, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_init_state(const LayoutDev& L, const double* amps, const long long* row_sample,
-                              int rows, int deterministic, T* psi, cudaStream_t st);
+                              const int* row_flag, const int2* row_win, int rows,
+                              int deterministic, T* S0, T* S1, double* integral, double* survival,
+                              cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_step(const HamDev<T>& H, const FieldDev<T>* fields, const int* row_field,
-                        const int* row_nmacro, long long macro, int rows, const T* cur,
-                        const T* prev, T* next, T* acc, T* X, const T* coef, int n_c, int n,
-                        int mode, cudaStream_t st);
+                        const int2* row_win, int macro, int rows, const T* cur, const T* prev,
+                        T* next, T* acc, T* X, const T* coef, int n_c, int n, int mode,
+                        cudaStream_t st);
 
 // integral[r] += sum_nm W_nm <x_n|x_m> for the macro-step just finished
 // (x_n = singlet slices X[r][n], W per field); one FP64 atomic per CTA.
 template <typename T>
 cudaError_t launch_gram_integrate(const T* X, const double* W, const int* row_field,
-                                  const int* row_nmacro, long long macro, int rows, long long Z,
-                                  int n_c, double* integral, cudaStream_t st);
+                                  const int2* row_win, int macro, int rows, long long Z, int n_c,
+                                  double* integral, cudaStream_t st);
 
 template <typename T>
-cudaError_t launch_norm(const T* S0, const T* S1, const int* row_nmacro, int rows, long long Z,
-                        double* survival, cudaStream_t st);
+cudaError_t launch_norm(const T* S0, const T* S1, const int2* row_win, const int* row_flag,
+                        int rows, long long Z, double* survival, cudaStream_t st);
 
 cudaError_t launch_finalize(const RowsDev& R, int rows, double k_S, double* per_sample,
                             cudaStream_t st);
 
-cudaError_t launch_stats(const double* per_sample, int n_fields, long long M, double* out,
-                         cudaStream_t st);
+// out[f] = (mean phi_S, mean phi_T, SE_S, SE_T, mean survival) over
+// per_sample[off[f] .. off[f] + cnt[f]).
+cudaError_t launch_stats(const double* per_sample, const long long* off, const long long* cnt,
+                         int n_fields, double* out, cudaStream_t st);
 
 cudaError_t launch_zero(double* p, size_t n, cudaStream_t st);
 

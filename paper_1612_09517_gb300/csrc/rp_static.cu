@@ -175,13 +175,14 @@ rp_status run_static(const rp::HostSystem& hs, int n_fields, const double* field
   // scratch budget: fixed per-call part plus rows
   const size_t vec = (size_t)Z * 8;
   const size_t fixed = up256((size_t)items * 3 * sizeof(double)) + up256((size_t)n_fields * 5 * sizeof(double)) +
+                       up256(2 * (size_t)n_fields * sizeof(long long)) +
                        up256((size_t)n_fields * sizeof(rp::FieldDev<T>)) +
                        up256((size_t)n_fields * n_c * 2 * sizeof(T)) +
                        up256((size_t)n_fields * n_c * n_c * 2 * sizeof(double));
   auto rows_bytes = [&](size_t R) {
     return 4 * up256(R * vec * sizeof(T)) + up256(R * n_c * Z * 2 * sizeof(T)) +
-           up256(R * rp::kMaxNucDev * 20 * sizeof(double)) +
-           2 * up256(R * sizeof(int)) + 2 * up256(R * sizeof(long long)) + up256(2 * R * sizeof(double));
+           up256(R * rp::kMaxNucDev * 20 * sizeof(double)) + up256(R * sizeof(int)) +
+           up256(R * sizeof(int2)) + 2 * up256(R * sizeof(long long)) + up256(2 * R * sizeof(double));
   };
   if (fixed + rows_bytes(1) > kStaticScratchBytes)
     return sfail(RP_EINVAL, "rp_yields_static needs " + std::to_string(fixed + rows_bytes(1)) +
@@ -193,6 +194,7 @@ rp_status run_static(const rp::HostSystem& hs, int n_fields, const double* field
   Bump b{scratch};
   double* d_ps = b.get<double>((size_t)items * 3);
   double* d_stats = b.get<double>((size_t)n_fields * 5);
+  long long* d_offcnt = b.get<long long>(2 * (size_t)n_fields);
   auto* d_fdev = b.get<rp::FieldDev<T>>(n_fields);
   T* d_coef = b.get<T>((size_t)n_fields * n_c * 2);
   double* d_W = b.get<double>((size_t)n_fields * n_c * n_c * 2);
@@ -203,7 +205,7 @@ rp_status run_static(const rp::HostSystem& hs, int n_fields, const double* field
   T* X = b.get<T>(R * n_c * Z * 2);
   double* amps = b.get<double>(R * rp::kMaxNucDev * 20);
   int* d_field = b.get<int>(R);
-  int* d_nmacro = b.get<int>(R);
+  int2* d_win = b.get<int2>(R);
   long long* d_sample = b.get<long long>(R);
   long long* d_out = b.get<long long>(R);
   double* d_int = b.get<double>(2 * R);
@@ -239,7 +241,8 @@ rp_status run_static(const rp::HostSystem& hs, int n_fields, const double* field
 
   const rp::HamDev<T> H = ham_of<T>(hs);
   const rp::LayoutDev L = layout_of(hs);
-  std::vector<int> h_field(R), h_nmacro(R);
+  std::vector<int> h_field(R);
+  std::vector<int2> h_win(R);
   std::vector<long long> h_sample(R), h_out(R);
   for (long long b0 = 0; b0 < items; b0 += (long long)R) {
     const int rows = (int)std::min<long long>((long long)R, items - b0);
@@ -249,30 +252,34 @@ rp_status run_static(const rp::HostSystem& hs, int n_fields, const double* field
       const int f = forder[it / Mr];
       const long long s = it % Mr;
       h_field[r] = f;
-      h_nmacro[r] = (int)plans[f].n_macro;
+      h_win[r] = make_int2(0, (int)plans[f].n_macro);
       h_sample[r] = o.deterministic ? s : o.sample_offset + s;
       h_out[r] = (long long)f * Mr + s;
       max_macro = std::max<long long>(max_macro, plans[f].n_macro);
     }
     sck(cudaMemcpyAsync(d_field, h_field.data(), rows * sizeof(int), cudaMemcpyHostToDevice, st), "h2d");
-    sck(cudaMemcpyAsync(d_nmacro, h_nmacro.data(), rows * sizeof(int), cudaMemcpyHostToDevice, st), "h2d");
+    sck(cudaMemcpyAsync(d_win, h_win.data(), rows * sizeof(int2), cudaMemcpyHostToDevice, st), "h2d");
     sck(cudaMemcpyAsync(d_sample, h_sample.data(), rows * sizeof(long long), cudaMemcpyHostToDevice, st), "h2d");
     sck(cudaMemcpyAsync(d_out, h_out.data(), rows * sizeof(long long), cudaMemcpyHostToDevice, st), "h2d");
-    h2d += (long long)rows * (2 * sizeof(int) + 2 * sizeof(long long));
+    h2d += (long long)rows * (sizeof(int) + sizeof(int2) + 2 * sizeof(long long));
+    // the array keeps the previous call's contents: integrals restart at zero
     L1(rp::launch_zero(d_int, 2 * R, st), "zero integrals");
     if (!o.deterministic)
-      L1(rp::launch_coherent_amps(L, d_sample, rows, seed, o.pair_id, amps, nullptr, st), "amplitudes");
-    L1(rp::launch_init_state<T>(L, amps, d_sample, rows, o.deterministic, S0, st), "initial states");
+      L1(rp::launch_coherent_amps(L, d_sample, nullptr, rows, seed, o.pair_id, amps, nullptr, st),
+         "amplitudes");
+    L1(rp::launch_init_state<T>(L, amps, d_sample, nullptr, d_win, rows, o.deterministic, S0, S1,
+                                nullptr, nullptr, st),
+       "initial states");
     T* Sb[2] = {S0, S1};
     for (long long k = 0; k < max_macro; ++k) {
       T* P = Sb[k & 1];
       T* Q = Sb[(k + 1) & 1];
       T* phi[3] = {P, F1, F2};
       long long act = 0;
-      for (int r = 0; r < rows; ++r) act += (k < h_nmacro[r]) ? 1 : 0;
+      for (int r = 0; r < rows; ++r) act += (k < h_win[r].y) ? 1 : 0;
       for (int n = 1; n < n_c; ++n) {
         const int mode = (n == 1) ? rp::MODE_FIRST : (n == n_c - 1 ? rp::MODE_LAST : rp::MODE_MID);
-        L1(rp::launch_step<T>(H, d_fdev, d_field, d_nmacro, k, rows, phi[(n - 1) % 3],
+        L1(rp::launch_step<T>(H, d_fdev, d_field, d_win, (int)k, rows, phi[(n - 1) % 3],
                               n >= 2 ? phi[(n - 2) % 3] : nullptr,
                               mode == rp::MODE_LAST ? nullptr : phi[n % 3], Q, X, d_coef, n_c, n,
                               mode, st),
@@ -280,14 +287,23 @@ rp_status run_static(const rp::HostSystem& hs, int n_fields, const double* field
         steps++;
       }
       row_terms += act * n_c;
-      L1(rp::launch_gram_integrate<T>(X, d_W, d_field, d_nmacro, k, rows, Z, n_c, d_int, st),
+      L1(rp::launch_gram_integrate<T>(X, d_W, d_field, d_win, (int)k, rows, Z, n_c, d_int, st),
          "gram-integral kernel");
     }
-    L1(rp::launch_norm<T>(S0, S1, d_nmacro, rows, Z, d_surv, st), "norm kernel");
-    rp::RowsDev RD{d_field, d_nmacro, d_sample, d_out, d_int, d_surv};
+    L1(rp::launch_norm<T>(S0, S1, d_win, nullptr, rows, Z, d_surv, st), "norm kernel");
+    rp::RowsDev RD{d_field, d_win, d_sample, d_out, nullptr, d_int, d_surv};
     L1(rp::launch_finalize(RD, rows, hs.k_S, d_ps, st), "finalize kernel");
   }
-  L1(rp::launch_stats(d_ps, n_fields, Mr, d_stats, st), "stats kernel");
+  {
+    std::vector<long long> offcnt(2 * (size_t)n_fields);
+    for (int f = 0; f < n_fields; ++f) {
+      offcnt[f] = (long long)f * Mr;
+      offcnt[n_fields + f] = Mr;
+    }
+    sck(cudaMemcpyAsync(d_offcnt, offcnt.data(), offcnt.size() * sizeof(long long), cudaMemcpyHostToDevice, st), "h2d");
+    h2d += (long long)(offcnt.size() * sizeof(long long));
+    L1(rp::launch_stats(d_ps, d_offcnt, d_offcnt + n_fields, n_fields, d_stats, st), "stats kernel");
+  }
   sck(cudaMemcpyAsync(out, d_stats, (size_t)n_fields * 5 * sizeof(double), cudaMemcpyDeviceToHost, st), "d2h");
   d2h += (long long)n_fields * 5 * sizeof(double);
   if (per_sample) {

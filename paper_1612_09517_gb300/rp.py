@@ -85,6 +85,10 @@ SIGNATURES = [
                              C.c_void_p]),
     ("rp_init_states", C.c_int, [C.c_void_p, C.c_int, C.c_uint64, C.c_uint32, C.c_longlong,
                                  C.c_int, C.c_void_p, C.POINTER(C.c_double), C.c_void_p]),
+    ("rp_yields_converged", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_double,
+                                      C.c_int, C.c_int, C.c_uint64, C.c_double,
+                                      C.POINTER(rp_options), C.POINTER(C.c_double),
+                                      C.POINTER(C.c_int), C.POINTER(rp_stats)]),
     ("rp_yields_static", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_int,
                                    C.c_uint64, C.c_double, C.POINTER(rp_options),
                                    C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -184,6 +188,20 @@ def rp_yields(h, fields, M, seed, t_max, opt=None, per_sample=False, Z=None):
     return res
 
 
+def rp_yields_converged(h, fields, se_target, M_min, M_max, seed, t_max, opt=None):
+    fields = np.ascontiguousarray(fields, dtype=np.float64).reshape(-1)
+    nf = fields.size
+    o = opt if opt is not None else rp_default_options()
+    out = np.zeros(max(nf * 5, 1))
+    used = np.zeros(max(nf, 1), dtype=np.int32)
+    stats = rp_stats()
+    _check(LIB.rp_yields_converged(h, nf, _dptr(fields), float(se_target), int(M_min), int(M_max),
+                                   C.c_uint64(int(seed)), float(t_max), C.byref(o), _dptr(out),
+                                   used.ctypes.data_as(C.POINTER(C.c_int)), C.byref(stats)))
+    return {"out": out[: nf * 5].reshape(nf, 5), "M_used": used[:nf].copy(),
+            "stats": stats.as_dict()}
+
+
 def rp_yields_static(h, fields, M, seed, t_max, opt=None, per_sample=False, Z=None):
     """rp_yields with all device scratch in the library's fixed 64 MiB array
     (for callers that must not allocate device memory while they run)."""
@@ -265,6 +283,10 @@ class System:
     def yields(self, fields, M, seed, t_max, per_sample=False, **opt):
         o = rp_default_options(**opt)
         return rp_yields(self.handle, fields, M, seed, t_max, o, per_sample, Z=self.Z)
+
+    def yields_converged(self, fields, se_target, M_min, M_max, seed, t_max, **opt):
+        o = rp_default_options(**opt)
+        return rp_yields_converged(self.handle, fields, se_target, M_min, M_max, seed, t_max, o)
 
     def to_input_order(self, psi):
         """Permute library-layout state vectors (..., 4Z) to the oracle's kron order

@@ -234,3 +234,26 @@ def test_config2_full_size_sampled(prec):
         # phi_T comes from conservation: error on the scale of the yields
         assert abs(got[1] - ref[1]) < TOL[prec] * max(abs(ref[1]), abs(ref[0]))
         assert abs(got[2] - ref[2]) < TOL[prec]
+
+
+# ----------------------------------------------- converged curve (Eq. 23 target)
+
+def test_converged_curve_meets_target_and_matches_plain_runs():
+    """rp_yields_converged: every field reaches SE <= target (or M_max), and each
+    field's estimate equals rp_yields over the same sample indices 0..M_f-1."""
+    rp = _rp()
+    s = wl.random_isotropic(3, 1, k_S=1.0, k_T=1.0, seed=21)
+    sy = rp.System(s)
+    fields = np.array([0.0, 1.0, 3.0, 8.0])
+    se_target, M_min, M_max = 4e-3, 8, 600
+    r = sy.yields_converged(fields, se_target, M_min, M_max, 5, 3.0, precision="fp64", max_rows=37)
+    used = r["M_used"]
+    assert np.all(used >= M_min) and np.all(used <= M_max)
+    for i, B in enumerate(fields):
+        assert r["out"][i, 2] <= se_target or used[i] == M_max
+        plain = sy.yields([B], int(used[i]), 5, 3.0, precision="fp64")
+        assert np.allclose(r["out"][i], plain["out"][0], rtol=1e-12, atol=1e-14)
+    # the oracle agrees on the samples it can check cheaply
+    psi0 = coherent.sample_states(s, 5, range(int(used[0])))
+    phS, _, _ = dense.sample_yields(s, fields[0], 3.0, psi0)
+    assert abs(r["out"][0, 0] - phS.mean()) < 1e-10
