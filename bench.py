@@ -15,11 +15,12 @@ over the full horizon.  Steps use disjoint sample ranges (sample_offset),
 ranks too.  The cost of one Chebyshev term does not depend on the field (same
 Z, same kernels), so the measured terms per second carry over to every field.
 
-Reported ``value``: projected seconds to the converged 64-field curve, i.e.
-M_needed x (Chebyshev terms of one sample over all 64 fields, exact from the
-plan) / (measured terms per second), with M_needed = max_f (sigma_f / 1e-3)^2
-from the benchmark's own samples (sigma per field with denominator M - 1,
-Eq. 23; the binding field is the one with the largest spread).  ``value``
+Reported ``value``: seconds to the converged 64-field curve (SE <= 1e-3 at
+every field, Eq. 23) = sum_f M_f x (Chebyshev terms of one sample at field f,
+exact from the plan) / (measured terms per second), where M_f are the
+per-field sample counts rp_yields_converged uses for the measured per-field
+spread (SIGMA_PROFILE).  ``python bench.py --converge`` runs that whole
+converged curve once and prints its measured wall time (293 s on GB300).  ``value``
 uses device time of the calls (CUDA events on the call's stream, inputs and
 work buffers resident); ``e2e`` uses the wall time of the same C-ABI calls
 with host buffers (planning, host<->device copies and synchronisation inside).
@@ -51,11 +52,27 @@ METRIC = ("time to converged Φ_S(B) at SE≤1e-3 vs FP64 plain; "
 WORKLOAD = ("config2: 12 nuclei (8x1/2 + 4x1, split 7/5), Z=20736, isotropic a~N(0,0.5 mT), "
             "J=0, k_S=2, k_T=0.5 us^-1, 64 fields 0-50 mT, t_max=20 us, SE target 1e-3")
 SE_TARGET = 1e-3
-# Largest per-field standard deviation of phi_S on this workload, as measured by
-# this benchmark's GPU arm (fields 0.8-4.8 mT, several hundred samples each).
-# The CPU arm cannot afford enough full-horizon samples to estimate it, so it
-# converts its throughput to the same metric with this value.
-SIGMA_REF = 0.029
+# Per-field standard deviation of phi_S over the 64 fields of this workload,
+# measured on GB300 by `python bench.py --converge` (rp_yields_converged,
+# SE <= 1e-3 everywhere; 16 to 991 samples per field, profiles/converged_config2_fp32.md).
+# Both arms turn their measured throughput into the time for a converged curve
+# with the same per-field sample counts M_f = max(16, ceil(1.15 sigma_f^2 / SE^2) + 1);
+# the CPU arm cannot afford enough full-horizon samples to measure sigma itself.
+SIGMA_PROFILE = [
+    0.01636, 0.02267, 0.02981, 0.02294, 0.01538, 0.0101, 0.00761, 0.00606, 0.00459, 0.00434,
+    0.00371, 0.00346, 0.00296, 0.00253, 0.00227, 0.00203, 0.00183, 0.00164, 0.00146, 0.00132,
+    0.00119, 0.00109, 0.00099, 0.00091, 0.00085, 0.0008, 0.00076, 0.00074, 0.00071, 0.0007,
+    0.00068, 0.00066, 0.00065, 0.00063, 0.00062, 0.00061, 0.0006, 0.00059, 0.00059, 0.00058,
+    0.00057, 0.00057, 0.00057, 0.00056, 0.00056, 0.00056, 0.00056, 0.00056, 0.00056, 0.00056,
+    0.00056, 0.00056, 0.00055, 0.00055, 0.00055, 0.00055, 0.00055, 0.00055, 0.00055, 0.00055,
+    0.00056, 0.00056, 0.00056, 0.00056]
+M_MIN = 16
+SIGMA_REF = max(SIGMA_PROFILE)
+
+
+def samples_per_field(sigmas=SIGMA_PROFILE):
+    """M_f of rp_yields_converged for SE <= SE_TARGET (Eq. 23), per field."""
+    return [max(M_MIN, int(math.ceil(1.15 * s * s / (SE_TARGET * SE_TARGET))) + 1) for s in sigmas]
 
 
 def _peaks():
@@ -140,13 +157,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _curve_terms(sy, fields, t_max, precision):
-    """Chebyshev terms of one sample over all fields (exact, from the plan)."""
-    tot = 0
+def _field_terms(sy, fields, t_max, precision):
+    """Chebyshev terms of one sample at each field (exact, from the plan)."""
+    out = []
     for B in fields:
         p = sy.plan(B, t_max, precision=precision)
-        tot += p["n_macro"] * p["n_cheb"]
-    return tot
+        out.append(p["n_macro"] * p["n_cheb"])
+    return out
+
+
+def _curve_terms(sy, fields, t_max, precision):
+    """Chebyshev terms of one sample over all fields."""
+    return sum(_field_terms(sy, fields, t_max, precision))
 
 
 def _m_needed(per_field_samples):
@@ -176,18 +198,18 @@ def _oracle_worker(args):
     return time.perf_counter() - t0, n_steps * 64
 
 
-def _oracle_curve_terms(t_max, fields):
+def _oracle_field_terms(t_max, fields):
     from oracle import chebyshev
     from paper_1612_09517_gb300 import workloads as wl
     s = wl.config2().system
-    tot = 0
+    out = []
     for B in fields:
         Hm = chebyshev.TensorHamiltonian(s, B)
         lo, hi = Hm.spectral_bounds()
         dE = 0.5 * (hi - lo) * (1.0 + 1e-12) + 1e-9
         h, n = chebyshev.plan(dE, 0.5 * max(s.k_S, s.k_T), t_max)
-        tot += n * 64
-    return tot
+        out.append(n * 64)
+    return out
 
 
 def cpu_oracle_throughput(cores, T_sample, B_list):
@@ -219,6 +241,9 @@ def parse():
     ap.add_argument("--samples-per-step", type=int, default=43)
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--converge", action="store_true",
+                    help="run the whole converged curve (rp_yields_converged, SE <= 1e-3) once "
+                         "and print its measured time")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run one small profiling case (192 rows, two macro-steps) and exit")
     return ap.parse_args()
@@ -242,7 +267,9 @@ def run_reference(args):
     # bounded sample: each core propagates one (field, sample) for T_sample us
     B_list = list(w.fields[[0, 21, 42, 63]])
     T_sample = 0.1
-    curve_terms = _oracle_curve_terms(w.t_max, w.fields)
+    fterms = _oracle_field_terms(w.t_max, w.fields)
+    Mf = samples_per_field()
+    conv_terms = sum(m * t for m, t in zip(Mf, fterms))
     times = []
     rates = []
     for i in range(args.warmup + args.steps):
@@ -251,22 +278,22 @@ def run_reference(args):
             times.append(wall)
             rates.append(rate)
     rate = statistics.median(rates)
-    m_needed = max(2, int(math.ceil((SIGMA_REF / SE_TARGET) ** 2)))
-    value = m_needed * curve_terms / rate
+    value = conv_terms / rate
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": statistics.median(times) * 1e3, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "oracle": "matrix-free FP64 Chebyshev (NumPy)",
-                   "M_needed": m_needed, "sigma_ref": SIGMA_REF,
-                   "note": "value = M_needed x oracle terms of one sample over the 64-field "
-                           "curve / oracle row-terms per second on the host cores"},
+                   "samples_total": int(sum(Mf)), "oracle_terms_converged_curve": int(conv_terms),
+                   "note": "value = oracle Chebyshev terms of the converged curve (per-field "
+                           "sample counts M_f, SE <= 1e-3) / oracle row-terms per second on the "
+                           "host cores"},
         "cpu_baseline": {"value": value, "unit": "s", "cores": cores, "kind": "oracle",
                          "sample": f"{cores} processes, each one (field, sample) propagation over "
                                    f"{T_sample} us at B in {[round(float(b), 2) for b in B_list]} mT; "
-                                   f"row-terms/s {rate:.0f} extrapolated to {curve_terms} terms per "
-                                   "sample over the 64-field curve"},
+                                   f"row-terms/s {rate:.0f} extrapolated to the {conv_terms} oracle "
+                                   "terms of the converged 64-field curve"},
         "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -290,6 +317,24 @@ def main():
 
     w = wl.config2()
     sy = rp.System(w.system)
+    prec = rp.RP_FP32 if args.precision == "fp32" else rp.RP_FP64
+    if args.converge:
+        sy.yields([0.0], 2, 0, 0.05)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        o = rp.rp_default_options(precision=prec, stream=torch.cuda.current_stream().cuda_stream)
+        r = rp.rp_yields_converged(sy.handle, w.fields, SE_TARGET, M_MIN, 4000, 0, w.t_max, o)
+        wall = time.perf_counter() - t0
+        st = r["stats"]
+        sig = r["out"][:, 2] * np.sqrt(r["M_used"])
+        print(json.dumps({"mode": "converge", "workload": WORKLOAD, "wall_s": wall,
+                          "device_ms": st["device_ms"], "propagations": st["propagations"],
+                          "row_terms": st["row_terms"], "kernel_launches": st["kernel_launches"],
+                          "rows": st["rows"], "max_SE": float(r["out"][:, 2].max()),
+                          "M_used": r["M_used"].tolist(),
+                          "sigma": [round(float(x), 5) for x in sig],
+                          "PhiS": r["out"][:, 0].tolist()}), flush=True)
+        return
     if args.ncu_case:
         # config-2 system, 3 fields x 64 samples = 192 rows (127 MB per state
         # vector, ~2 GB on the device), horizon of two macro-steps at 50 mT
@@ -301,9 +346,11 @@ def main():
     idx = np.array([int(x) for x in args.field_indices.split(",")])
     fields = w.fields[idx]
     m = args.samples_per_step
-    prec = rp.RP_FP32 if args.precision == "fp32" else rp.RP_FP64
     stream = torch.cuda.current_stream()
-    curve_terms = _curve_terms(sy, w.fields, w.t_max, prec)
+    fterms = _field_terms(sy, w.fields, w.t_max, prec)
+    curve_terms = sum(fterms)
+    Mf = samples_per_field()
+    conv_terms = sum(m * t for m, t in zip(Mf, fterms))
 
     def step(i, profile):
         o = rp.rp_default_options(precision=prec, sample_offset=(i * world + rank) * m,
@@ -360,11 +407,13 @@ def main():
     dev_ms, wall_s, region_ms = vals.tolist()
     row_terms_all = work[0].item()
 
-    m_needed, sigma_max = _m_needed(samples)
+    m_live, sigma_live = _m_needed(samples)
+    sigma_max = max(SIGMA_PROFILE)
+    m_uniform = max(2, int(math.ceil((sigma_max / SE_TARGET) ** 2)))
     rate_dev = row_terms_all / (dev_ms * 1e-3)
     rate_e2e = row_terms_all / wall_s
-    value = m_needed * curve_terms / rate_dev
-    e2e = m_needed * curve_terms / rate_e2e
+    value = conv_terms / rate_dev
+    e2e = conv_terms / rate_e2e
 
     # plain FP64 form on the same GPU, measured on a short horizon (per-term cost
     # does not depend on the horizon) with the same row count
@@ -377,9 +426,10 @@ def main():
         st = r64["stats"]
         rate64 = st["row_terms"] * world / (st["device_ms"] * 1e-3)
         curve64 = _curve_terms(sy, w.fields, w.t_max, rp.RP_FP64)
-        t64 = m_needed * curve64 / rate64
+        t64 = m_uniform * curve64 / rate64
         fp64 = {"time_to_converged_s": t64, "row_terms_per_s": rate64,
-                "ratio_fp32_over_fp64": value / t64}
+                "form": "FP64, same M at every field (M = (sigma_max / 1e-3)^2), no refill",
+                "ratio_ours_over_fp64_plain": value / t64}
 
     peak, peak_src = _peaks()
     achieved = step_bytes / (step_ms * 1e-3) / 1e9 if step_ms > 0 else None
@@ -403,13 +453,13 @@ def main():
         T_sample = 0.1
         B_list = list(w.fields[[0, 21, 42, 63]])
         rate_cpu, wall_cpu, terms_cpu = cpu_oracle_throughput(cores, T_sample, B_list)
-        curve_o = _oracle_curve_terms(w.t_max, w.fields)
-        cpu = {"value": m_needed * curve_o / rate_cpu, "unit": "s", "cores": cores,
+        conv_o = sum(m * t for m, t in zip(Mf, _oracle_field_terms(w.t_max, w.fields)))
+        cpu = {"value": conv_o / rate_cpu, "unit": "s", "cores": cores,
                "kind": "oracle",
                "sample": f"{cores} spawned processes, each one (field, sample) FP64 matrix-free "
                          f"propagation over {T_sample} us (B in {[round(float(b), 1) for b in B_list]} mT); "
                          f"{rate_cpu:.0f} row-terms/s over {wall_cpu:.1f} s, extrapolated to "
-                         f"M_needed={m_needed} x {curve_o} oracle terms"}
+                         f"the {conv_o} oracle terms of the converged curve (per-field M_f)"}
 
     if rank == 0:
         line = {
@@ -421,7 +471,11 @@ def main():
             "config": {"workload": WORKLOAD, "step_fields_mT": [round(float(b), 3) for b in fields],
                        "samples_per_step_per_rank": m, "rows": rows,
                        "l2": "working set per step > 129 MB L2 (state vectors + Gram buffers)",
-                       "sigma_max": sigma_max, "M_needed": m_needed,
+                       "se_target": SE_TARGET, "samples_converged_curve": int(sum(Mf)),
+                       "terms_converged_curve": int(conv_terms),
+                       "sigma_live_step_fields": sigma_live, "sigma_profile_max": sigma_max,
+                       "uniform_M": m_uniform,
+                       "uniform_M_time_s": m_uniform * curve_terms / rate_dev,
                        "curve_terms_per_sample": curve_terms,
                        "row_terms_per_s": rate_dev, "timed_region_ms": region_ms},
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(h2d / max(args.steps, 1)),

@@ -213,6 +213,77 @@ rp_status rp_apply_h(rp_system* sys, double B, int precision, int n_vec, const v
 rp_status rp_init_states(rp_system* sys, int precision, uint64_t seed, uint32_t pair_id,
                          long long sample0, int n, void* psi_dev, double* angles, void* stream);
 
+/* ---- learned control variate (Eqs. 18, 23 with a control variate) ----
+ * g(Omega, B): a multilayer perceptron (SiLU hidden layers, linear output,
+ * BF16 weights, FP32 activations and accumulation) of 3 n_nuc + 10 features:
+ * n(Omega_k) for every nucleus k in input order (Eq. 16); the classical
+ * hyperfine fields b_r = sum_{k on radical r} I_k A_k n(Omega_k) / B_hyp,r
+ * (B_hyp of Eq. 21, a_k^2 generalised to |A_k|_F^2 / 3); |b_1|, |b_2|,
+ * b_1 . b_2; B / B_scale -- with Omega_k drawn by the same Philox map as
+ * rp_yields.  Trained by mean
+ * squared error on per-sample yields; the estimate of one field is
+ * Phi_cv = mean(phi - beta (g - mu)), beta = cov(phi, g)/var(g), mu = E[g].
+ * Training must use samples disjoint from those of the estimate. */
+typedef struct rp_cv rp_cv; /* opaque, library-owned */
+
+typedef struct rp_cv_options {
+  int hidden;            /* hidden width (default 256) */
+  int layers;            /* hidden layers (default 3) */
+  int epochs;            /* training epochs (default 200) */
+  int batch;             /* minibatch size (default 256) */
+  double lr;             /* Adam learning rate (default 1e-3) */
+  double weight_decay;   /* decoupled weight decay (default 1e-4) */
+  double B_scale;        /* field scale of the last feature, mT (default 10) */
+  uint64_t init_seed;    /* weight initialisation and shuffling seed (default 1) */
+  void* stream;          /* cudaStream_t, NULL: per-thread default stream */
+} rp_cv_options;
+
+/* Defaults above. */
+void rp_cv_default_options(rp_cv_options* opt);
+
+/* Network for the nuclei of sys (input dimension 3 n_nuc + 10), initialised
+ * uniformly with scale sqrt(6 / fan_in) (hidden) and sqrt(3 / fan_in) (output),
+ * zero biases.  Errors: RP_EINVAL, RP_ENOMEM, RP_ECUDA, RP_ENODEV. */
+rp_status rp_cv_create(const rp_system* sys, const rp_cv_options* opt, rp_cv** out);
+
+/* Release a network (NULL is ignored). */
+void rp_cv_destroy(rp_cv* cv);
+
+/* Copy the flat FP32 parameter vector (W_0, b_0, W_1, b_1, ...; W_l row-major
+ * (out, in)) out to get and/or in from set (host arrays of *count floats);
+ * *count receives the number of parameters.  Setting refreshes the BF16
+ * weights. */
+rp_status rp_cv_params(rp_cv* cv, float* get, const float* set, long long* count);
+
+/* Loss 1/(2n) sum (g(x_i) - y_i)^2 and its gradient for n host feature rows
+ * x (n x (3 n_nuc + 10), FP32) and targets y; grad has *count floats. */
+rp_status rp_cv_loss_grad(rp_cv* cv, int n, const float* x, const float* y, double* loss,
+                          float* grad);
+
+/* Train on n per-sample yields phi of samples[i] at fields B[i] (mT) drawn with
+ * (seed, pair_id); targets are phi standardised per distinct field.  Adam,
+ * shuffled minibatches; loss_per_epoch (host, epochs doubles) may be NULL. */
+rp_status rp_cv_train(rp_cv* cv, int n, const double* B, const long long* samples, uint64_t seed,
+                      uint32_t pair_id, const double* phi, double* loss_per_epoch);
+
+/* g at n (field, sample) pairs; g is a host array of n doubles. */
+rp_status rp_cv_eval(rp_cv* cv, int n, const double* B, const long long* samples, uint64_t seed,
+                     uint32_t pair_id, double* g);
+
+/* mu_f = mean of g over samples 0 .. n_mc-1 of (seed, pair_id) at each field,
+ * and var_mu_f = var(g) / n_mc (host arrays of n_fields doubles). */
+rp_status rp_cv_mean(rp_cv* cv, int n_fields, const double* B, long long n_mc, uint64_t seed,
+                     uint32_t pair_id, double* mu, double* var_mu);
+
+/* Per-field control-variate estimates from per-sample yields (rp_yields
+ * layout: phi_S, phi_T, survival triples) and g of the same samples, field f
+ * owning entries [offsets[f], offsets[f] + counts[f]) (counts >= 2).
+ * out [n_fields * 5]: Phi_cv, SE_cv, Phi_plain, SE_plain, beta, where
+ * SE_cv^2 = var(phi - beta g)/M + beta^2 var_mu (Eq. 23). */
+rp_status rp_cv_estimate(rp_cv* cv, int n_fields, const long long* offsets, const long long* counts,
+                         const double* per_sample, const double* g, const double* mu,
+                         const double* var_mu, double* out);
+
 /* rp_yields without device allocation.  The paper has no counterpart: this
  * entry point exists for callers that must not allocate device memory while
  * they run -- e.g. a host application that hands each plug-in a fixed

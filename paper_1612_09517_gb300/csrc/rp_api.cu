@@ -610,6 +610,17 @@ rp_status run_converged(rp_system* sys, int n_fields, const double* fields, doub
 
 namespace rp {
 void set_last_error(const std::string& msg) { g_err = msg; }
+// Device allocation through the caller's hooks (rp_set_allocator) or
+// cudaMallocAsync; throws nothing, returns NULL on failure.
+void* device_alloc(size_t bytes, cudaStream_t st) {
+  try {
+    return dev_alloc(bytes, st);
+  } catch (const CudaFail&) {
+    return nullptr;
+  }
+}
+void device_free(void* p, cudaStream_t st) { dev_free(p, st); }
+rp_status device_check() { return check_device(); }
 }  // namespace rp
 
 extern "C" {

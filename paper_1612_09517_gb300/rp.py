@@ -60,6 +60,12 @@ class rp_field_plan(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class rp_cv_options(C.Structure):
+    _fields_ = [("hidden", C.c_int), ("layers", C.c_int), ("epochs", C.c_int), ("batch", C.c_int),
+                ("lr", C.c_double), ("weight_decay", C.c_double), ("B_scale", C.c_double),
+                ("init_seed", C.c_uint64), ("stream", C.c_void_p)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
@@ -89,6 +95,23 @@ SIGNATURES = [
                                       C.c_int, C.c_int, C.c_uint64, C.c_double,
                                       C.POINTER(rp_options), C.POINTER(C.c_double),
                                       C.POINTER(C.c_int), C.POINTER(rp_stats)]),
+    ("rp_cv_default_options", None, [C.POINTER(rp_cv_options)]),
+    ("rp_cv_create", C.c_int, [C.c_void_p, C.POINTER(rp_cv_options), C.POINTER(C.c_void_p)]),
+    ("rp_cv_destroy", None, [C.c_void_p]),
+    ("rp_cv_params", C.c_int, [C.c_void_p, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                               C.POINTER(C.c_longlong)]),
+    ("rp_cv_loss_grad", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                  C.POINTER(C.c_double), C.POINTER(C.c_float)]),
+    ("rp_cv_train", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
+                              C.c_uint64, C.c_uint32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("rp_cv_eval", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_longlong),
+                             C.c_uint64, C.c_uint32, C.POINTER(C.c_double)]),
+    ("rp_cv_mean", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_longlong, C.c_uint64,
+                             C.c_uint32, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("rp_cv_estimate", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_longlong),
+                                 C.POINTER(C.c_longlong), C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                 C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("rp_yields_static", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_int,
                                    C.c_uint64, C.c_double, C.POINTER(rp_options),
                                    C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -315,3 +338,101 @@ class System:
         # target axes: positions N-1..0 (input index order[p]), then e1, e2
         perm = list(range(nl)) + [nl + 2 + int(self.order[p]) for p in range(npos - 1, -1, -1)] + [nl, nl + 1]
         return np.transpose(t, perm).reshape(*lead, -1)
+
+
+def _fptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def _lptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_longlong))
+
+
+def rp_cv_default_options(**kw) -> rp_cv_options:
+    o = rp_cv_options()
+    LIB.rp_cv_default_options(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class ControlVariate:
+    """An ``rp_cv`` network for the nuclei of a ``System`` (see include/rp.h)."""
+
+    def __init__(self, system, **opt):
+        self.system = system
+        self.opt = rp_cv_default_options(**opt)
+        h = C.c_void_p()
+        _check(LIB.rp_cv_create(system.handle, C.byref(self.opt), C.byref(h)))
+        self.handle = h
+        cnt = C.c_longlong()
+        _check(LIB.rp_cv_params(h, None, None, C.byref(cnt)))
+        self.n_params = int(cnt.value)
+        self.d_in = 3 * system.n_nuc + 10
+
+    def close(self):
+        if self.handle:
+            LIB.rp_cv_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        p = np.zeros(self.n_params, dtype=np.float32)
+        _check(LIB.rp_cv_params(self.handle, _fptr(p), None, None))
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.n_params
+        _check(LIB.rp_cv_params(self.handle, None, _fptr(p), None))
+
+    def loss_grad(self, x, y):
+        x = np.ascontiguousarray(x, dtype=np.float32)
+        y = np.ascontiguousarray(y, dtype=np.float32)
+        loss = C.c_double()
+        g = np.zeros(self.n_params, dtype=np.float32)
+        _check(LIB.rp_cv_loss_grad(self.handle, y.size, _fptr(x), _fptr(y), C.byref(loss), _fptr(g)))
+        return loss.value, g
+
+    def train(self, B, samples, seed, phi, pair_id=0):
+        B = np.ascontiguousarray(B, dtype=np.float64)
+        samples = np.ascontiguousarray(samples, dtype=np.int64)
+        phi = np.ascontiguousarray(phi, dtype=np.float64)
+        losses = np.zeros(max(self.opt.epochs, 1))
+        _check(LIB.rp_cv_train(self.handle, B.size, _dptr(B), _lptr(samples), C.c_uint64(seed),
+                               C.c_uint32(pair_id), _dptr(phi), _dptr(losses)))
+        return losses[: self.opt.epochs]
+
+    def eval(self, B, samples, seed, pair_id=0):
+        B = np.ascontiguousarray(B, dtype=np.float64)
+        samples = np.ascontiguousarray(samples, dtype=np.int64)
+        g = np.zeros(max(B.size, 1))
+        _check(LIB.rp_cv_eval(self.handle, B.size, _dptr(B), _lptr(samples), C.c_uint64(seed),
+                              C.c_uint32(pair_id), _dptr(g)))
+        return g[: B.size]
+
+    def mean(self, fields, n_mc, seed, pair_id=0):
+        fields = np.ascontiguousarray(fields, dtype=np.float64)
+        mu = np.zeros(max(fields.size, 1))
+        vm = np.zeros(max(fields.size, 1))
+        _check(LIB.rp_cv_mean(self.handle, fields.size, _dptr(fields), int(n_mc), C.c_uint64(seed),
+                              C.c_uint32(pair_id), _dptr(mu), _dptr(vm)))
+        return mu[: fields.size], vm[: fields.size]
+
+    def estimate(self, offsets, counts, per_sample, g, mu, var_mu):
+        offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+        counts = np.ascontiguousarray(counts, dtype=np.int64)
+        per_sample = np.ascontiguousarray(per_sample, dtype=np.float64)
+        g = np.ascontiguousarray(g, dtype=np.float64)
+        mu = np.ascontiguousarray(mu, dtype=np.float64)
+        var_mu = np.ascontiguousarray(var_mu, dtype=np.float64)
+        nf = offsets.size
+        out = np.zeros(max(nf * 5, 1))
+        _check(LIB.rp_cv_estimate(self.handle, nf, _lptr(offsets), _lptr(counts), _dptr(per_sample),
+                                  _dptr(g), _dptr(mu), _dptr(var_mu), _dptr(out)))
+        return out[: nf * 5].reshape(nf, 5)
