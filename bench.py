@@ -56,7 +56,7 @@ SE_TARGET = 1e-3
 # measured on GB300 by `python bench.py --converge` (rp_yields_converged,
 # SE <= 1e-3 everywhere; 16 to 991 samples per field, profiles/converged_config2_fp32.md).
 # Both arms turn their measured throughput into the time for a converged curve
-# with the same per-field sample counts M_f = max(16, ceil(1.15 sigma_f^2 / SE^2) + 1);
+# with the same per-field sample counts M_f = max(8, ceil(1.15 sigma_f^2 / SE^2) + 1);
 # the CPU arm cannot afford enough full-horizon samples to measure sigma itself.
 SIGMA_PROFILE = [
     0.01636, 0.02267, 0.02981, 0.02294, 0.01538, 0.0101, 0.00761, 0.00606, 0.00459, 0.00434,
@@ -66,7 +66,7 @@ SIGMA_PROFILE = [
     0.00057, 0.00057, 0.00057, 0.00056, 0.00056, 0.00056, 0.00056, 0.00056, 0.00056, 0.00056,
     0.00056, 0.00056, 0.00055, 0.00055, 0.00055, 0.00055, 0.00055, 0.00055, 0.00055, 0.00055,
     0.00056, 0.00056, 0.00056, 0.00056]
-M_MIN = 16
+M_MIN = 8
 SIGMA_REF = max(SIGMA_PROFILE)
 
 
@@ -244,6 +244,8 @@ def parse():
     ap.add_argument("--converge", action="store_true",
                     help="run the whole converged curve (rp_yields_converged, SE <= 1e-3) once "
                          "and print its measured time")
+    ap.add_argument("--cv", action="store_true",
+                    help="with --converge: use the learned control variate (rp_yields_cv)")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run one small profiling case (192 rows, two macro-steps) and exit")
     return ap.parse_args()
@@ -323,6 +325,19 @@ def main():
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         o = rp.rp_default_options(precision=prec, stream=torch.cuda.current_stream().cuda_stream)
+        if args.cv:
+            plan = rp.rp_cv_default_plan()
+            r = rp.rp_yields_cv(sy.handle, w.fields, SE_TARGET, M_MIN, 4000, 0, w.t_max, o, plan)
+            wall = time.perf_counter() - t0
+            st = r["stats"]
+            print(json.dumps({"mode": "converge+cv", "workload": WORKLOAD, "wall_s": wall,
+                              "propagations": st["propagations"], "row_terms": st["row_terms"],
+                              "kernel_launches": st["kernel_launches"], "rows": st["rows"],
+                              "M_min": M_MIN, "max_SE": float(r["out"][:, 1].max()),
+                              "M_plain": r["M_plain"].tolist(), "M_cv": r["M_cv"].tolist(),
+                              "beta": [round(float(x), 5) for x in r["out"][:, 6]],
+                              "PhiS": r["out"][:, 0].tolist()}), flush=True)
+            return
         r = rp.rp_yields_converged(sy.handle, w.fields, SE_TARGET, M_MIN, 4000, 0, w.t_max, o)
         wall = time.perf_counter() - t0
         st = r["stats"]
@@ -330,7 +345,7 @@ def main():
         print(json.dumps({"mode": "converge", "workload": WORKLOAD, "wall_s": wall,
                           "device_ms": st["device_ms"], "propagations": st["propagations"],
                           "row_terms": st["row_terms"], "kernel_launches": st["kernel_launches"],
-                          "rows": st["rows"], "max_SE": float(r["out"][:, 2].max()),
+                          "rows": st["rows"], "M_min": M_MIN, "max_SE": float(r["out"][:, 2].max()),
                           "M_used": r["M_used"].tolist(),
                           "sigma": [round(float(x), 5) for x in sig],
                           "PhiS": r["out"][:, 0].tolist()}), flush=True)

@@ -188,8 +188,8 @@ rp_status rp_yields(rp_system* sys, int n_fields, const double* fields, int M, u
  * (the "SE <= target on the whole curve" criterion; Eqs. 18, 20, 22).
  * Each field first gets M_min coherent-state samples; then, in rounds, each
  * field whose standard error of Phi_S is above se_target gets the samples its
- * measured spread asks for, ceil(1.15 sigma_f^2 / se_target^2) + 1, capped at
- * M_max.  Sample s uses the same directions at every field.  All rounds run
+ * measured spread asks for, ceil(1.15 sigma_f^2 / se_target^2) + 1, at most 4x
+ * its samples so far per round, capped at M_max.  Sample s uses the same directions at every field.  All rounds run
  * on one pool of rows that are refilled as propagations finish.
  *   out     [n_fields * 5] host: Phi_S, Phi_T, SE_S, SE_T, mean survival
  *   M_used  [n_fields] host or NULL: samples used per field
@@ -197,6 +197,21 @@ rp_status rp_yields(rp_system* sys, int n_fields, const double* fields, int M, u
 rp_status rp_yields_converged(rp_system* sys, int n_fields, const double* fields, double se_target,
                               int M_min, int M_max, uint64_t seed, double t_max,
                               const rp_options* opt, double* out, int* M_used, rp_stats* stats);
+
+/* Yields of several radical pairs of uneven size in one call (the same
+ * quantities as rp_yields for each pair).  System s has n_fields[s] fields
+ * fields[s], M[s] >= 2 samples per field and horizon t_max[s]; it draws its
+ * directions with Philox pair word opt->pair_id + s, so its results equal
+ * those of rp_yields on that system with pair_id + s.  Systems are grouped by
+ * size (a row slot holds at most twice a system's Z) and each group runs all
+ * its (system, field, sample) propagations on one pool of rows that is
+ * refilled as propagations finish.
+ *   out[s]  [n_fields[s] * 5] host: Phi_S, Phi_T, SE_S, SE_T, mean survival
+ * opt->deterministic must be 0.  Errors as rp_yields. */
+rp_status rp_yields_batch(int n_sys, rp_system* const* systems, const int* n_fields,
+                          const double* const* fields, const int* M, const double* t_max,
+                          uint64_t seed, const rp_options* opt, double* const* out,
+                          rp_stats* stats);
 
 /* y = (H - iK) x for n_vec state vectors in the layout above, field B (mT);
  * x_dev and y_dev are device arrays of n_vec * 4Z complex values in the
@@ -283,6 +298,42 @@ rp_status rp_cv_mean(rp_cv* cv, int n_fields, const double* B, long long n_mc, u
 rp_status rp_cv_estimate(rp_cv* cv, int n_fields, const long long* offsets, const long long* counts,
                          const double* per_sample, const double* g, const double* mu,
                          const double* var_mu, double* out);
+
+/* Plan of rp_yields_cv. */
+typedef struct rp_cv_plan {
+  int M_train;        /* plain samples per control-variate field, used for training (default 300) */
+  int cv_threshold;   /* a field whose plain estimate would need at least this many
+                         samples uses the control variate (default 150) */
+  long long n_mc;     /* directions per field for mu = E[g] (default 2^18) */
+  rp_cv_options net;  /* network and training options (rp_cv_default_options) */
+} rp_cv_plan;
+
+/* Defaults above. */
+void rp_cv_default_plan(rp_cv_plan* plan);
+
+/* Singlet yields over a field sweep to a target standard error at every field,
+ * with the learned control variate where it pays (Eqs. 18, 20, 22, 23):
+ *  1. M_min plain samples (indices sample_offset + 0, 1, ...) at every field;
+ *     fields whose plain estimate would need fewer than
+ *     max(cv_threshold, 2 M_train) samples continue with plain rounds as
+ *     rp_yields_converged does (each round at most 4x the samples so far);
+ *  2. the other fields get plain samples up to M_train; one network is trained
+ *     on all of them (rp_cv_train) and mu = E[g] is computed per field from
+ *     n_mc directions of a separate stream (pair word with bit 30 set);
+ *  3. those fields then draw fresh samples (indices from 2^40 + sample_offset,
+ *     disjoint from the training samples, so the estimate stays unbiased),
+ *     estimate with the control variate (rp_cv_estimate) and combine it with
+ *     their plain estimate by inverse-variance weights until the combined SE
+ *     reaches se_target (or M_max samples).
+ *   out [n_fields * 8]: Phi_S, SE_S (combined), Phi_S and SE of the plain
+ *     samples, Phi_S and SE of the control-variate samples, beta, 1 if the
+ *     field used the control variate else 0
+ *   M_plain, M_cv [n_fields] host or NULL: samples of each kind per field
+ * opt->deterministic must be 0; sample_offset < 2^39.  Errors as rp_yields. */
+rp_status rp_yields_cv(rp_system* sys, int n_fields, const double* fields, double se_target,
+                       int M_min, int M_max, uint64_t seed, double t_max, const rp_options* opt,
+                       const rp_cv_plan* plan, double* out, int* M_plain, int* M_cv,
+                       rp_stats* stats);
 
 /* rp_yields without device allocation.  The paper has no counterpart: this
  * entry point exists for callers that must not allocate device memory while

@@ -159,10 +159,11 @@ double default_tol(int precision) { return precision == RP_FP64 ? 1e-15 : 1e-9; 
 
 // One work item: a (field, sample) propagation over the whole horizon.
 struct Item {
-  int field;
+  int field;         // index into the engine's per-field tables
   long long sample;  // Philox sample index, or basis index when deterministic
   long long out;     // slot in the per-sample output array
   int n_macro;       // macro-steps of its field's plan
+  int sys;           // index into the engine's systems
 };
 
 // Runs lists of work items on a pool of R rows: every row propagates one item
@@ -173,8 +174,35 @@ struct Item {
 template <typename T>
 class YieldEngine {
  public:
-  YieldEngine(const rp::HostSystem& hs, const rp_options& o, int n_c, cudaStream_t st, Arena& ar)
-      : hs_(hs), o_(o), n_c_(n_c), st_(st), ar_(ar), H_(make_ham<T>(hs)), L_(make_layout(hs)) {}
+  YieldEngine(const std::vector<const rp::HostSystem*>& systems, const rp_options& o, int n_c,
+              cudaStream_t st, Arena& ar, const std::vector<uint32_t>* pairs = nullptr)
+      : sys_(systems), o_(o), n_c_(n_c), st_(st), ar_(ar) {
+    const int ns = (int)systems.size();
+    std::vector<rp::HamDev<T>> ham(ns);
+    std::vector<rp::LayoutDev> lay(ns);
+    std::vector<double> kS(ns);
+    Zslot_ = 1;
+    ham1_ = make_ham<T>(*systems[0]);
+    for (int i = 0; i < ns; ++i) {
+      ham[i] = make_ham<T>(*systems[i]);
+      lay[i] = make_layout(*systems[i]);
+      kS[i] = systems[i]->k_S;
+      Zslot_ = std::max<long long>(Zslot_, systems[i]->Z);
+      aniso_ = aniso_ || systems[i]->aniso;
+    }
+    d_ham_ = ar_.get<rp::HamDev<T>>(ns);
+    d_lay_ = ar_.get<rp::LayoutDev>(ns);
+    d_kS_ = ar_.get<double>(ns);
+    ck(cudaMemcpyAsync(d_ham_, ham.data(), ns * sizeof(ham[0]), cudaMemcpyHostToDevice, st_), "h2d systems");
+    ck(cudaMemcpyAsync(d_lay_, lay.data(), ns * sizeof(lay[0]), cudaMemcpyHostToDevice, st_), "h2d systems");
+    ck(cudaMemcpyAsync(d_kS_, kS.data(), ns * sizeof(double), cudaMemcpyHostToDevice, st_), "h2d systems");
+    h2d += (long long)(ns * (sizeof(ham[0]) + sizeof(lay[0]) + sizeof(double)));
+    if (pairs) {
+      d_pair_ = ar_.get<uint32_t>(ns);
+      ck(cudaMemcpyAsync(d_pair_, pairs->data(), ns * sizeof(uint32_t), cudaMemcpyHostToDevice, st_), "h2d pairs");
+      h2d += (long long)(ns * sizeof(uint32_t));
+    }
+  }
 
   long long launches = 0, step_launches = 0, row_terms = 0, h2d = 0;
   double step_bytes_all = 0.0;
@@ -219,15 +247,19 @@ class YieldEngine {
     return (4 * (size_t)Z * 8 + (size_t)n_c * Z * 2) * sizeof(T) + 256 + rp::kMaxNucDev * 20 * 8;
   }
 
+  long long zslot() const { return Zslot_; }
+
   void alloc_rows(int R) {
     R_ = R;
-    const size_t vec = (size_t)hs_.Z * 8;
+    const size_t vec = (size_t)Zslot_ * 8;
     S0_ = ar_.get<T>((size_t)R * vec);
     S1_ = ar_.get<T>((size_t)R * vec);
     F1_ = ar_.get<T>((size_t)R * vec);
     F2_ = ar_.get<T>((size_t)R * vec);
-    X_ = ar_.get<T>((size_t)R * n_c_ * hs_.Z * 2);
+    X_ = ar_.get<T>((size_t)R * n_c_ * Zslot_ * 2);
     amps_ = ar_.get<double>((size_t)R * rp::kMaxNucDev * 10 * 2);
+    row_sys_ = ar_.get<int>(R);
+    S_ = rp::SysTab<T>{d_ham_, d_lay_, d_kS_, row_sys_, Zslot_, o_.pair_id, d_pair_};
     rows_.field = ar_.get<int>(R);
     rows_.win = ar_.get<int2>(R);
     rows_.sample = ar_.get<long long>(R);
@@ -240,7 +272,7 @@ class YieldEngine {
   void run(const std::vector<Item>& items, double* d_ps) {
     const int R = R_;
     const long long n_items = (long long)items.size();
-    std::vector<int> h_field(R, 0), h_flag(R, 0);
+    std::vector<int> h_field(R, 0), h_flag(R, 0), h_sys(R, 0);
     std::vector<int2> h_win(R, make_int2(0, 0));
     std::vector<long long> h_sample(R, 0), h_out(R, 0);
     long long next = 0;
@@ -251,6 +283,7 @@ class YieldEngine {
       h_win[r] = make_int2(k, k + it.n_macro);
       h_sample[r] = it.sample;
       h_out[r] = it.out;
+      h_sys[r] = it.sys;
       h_flag[r] = 1;
     };
     auto upload_rows = [&]() {
@@ -259,13 +292,14 @@ class YieldEngine {
       ck(cudaMemcpyAsync(rows_.sample, h_sample.data(), R * sizeof(long long), cudaMemcpyHostToDevice, st_), "h2d rows");
       ck(cudaMemcpyAsync(rows_.out, h_out.data(), R * sizeof(long long), cudaMemcpyHostToDevice, st_), "h2d rows");
       ck(cudaMemcpyAsync(rows_.flag, h_flag.data(), R * sizeof(int), cudaMemcpyHostToDevice, st_), "h2d rows");
-      h2d += (long long)R * (2 * sizeof(int) + sizeof(int2) + 2 * sizeof(long long));
+      ck(cudaMemcpyAsync(row_sys_, h_sys.data(), R * sizeof(int), cudaMemcpyHostToDevice, st_), "h2d rows");
+      h2d += (long long)R * (3 * sizeof(int) + sizeof(int2) + 2 * sizeof(long long));
     };
     auto init_flagged = [&]() {
       if (!o_.deterministic)
-        launched(rp::launch_coherent_amps(L_, rows_.sample, rows_.flag, R, seed_, o_.pair_id, amps_,
-                                          nullptr, st_), "coherent amplitudes");
-      launched(rp::launch_init_state<T>(L_, amps_, rows_.sample, rows_.flag, rows_.win, R,
+        launched(rp::launch_coherent_amps<T>(S_, rows_.sample, rows_.flag, R, seed_, amps_, nullptr,
+                                             st_), "coherent amplitudes");
+      launched(rp::launch_init_state<T>(S_, amps_, rows_.sample, rows_.flag, rows_.win, R,
                                         o_.deterministic, S0_, S1_, rows_.integral,
                                         rows_.survival, st_), "initial states");
     };
@@ -275,10 +309,15 @@ class YieldEngine {
     }
     upload_rows();
     init_flagged();
-    const double vbytes = (double)hs_.Z * 8 * sizeof(T);
     for (int k = 0; live > 0; ++k) {
       long long act = 0;
-      for (int r = 0; r < R; ++r) act += (h_win[r].x <= k && k < h_win[r].y) ? 1 : 0;
+      double act_z = 0.0;  // configurations of the active rows
+      for (int r = 0; r < R; ++r)
+        if (h_win[r].x <= k && k < h_win[r].y) {
+          ++act;
+          act_z += (double)sys_[h_sys[r]]->Z;
+        }
+      const double vbytes = 8.0 * sizeof(T) * act_z;  // one state vector of every active row
       T* Sb[2] = {S0_, S1_};
       T* P = Sb[k & 1];
       T* Q = Sb[(k + 1) & 1];
@@ -294,13 +333,14 @@ class YieldEngine {
       double bytes = 0.0;
       for (int n = 1; n < n_c_; ++n) {
         const int mode = (n == 1) ? rp::MODE_FIRST : (n == n_c_ - 1 ? rp::MODE_LAST : rp::MODE_MID);
-        launched(rp::launch_step<T>(H_, d_fdev_, rows_.field, rows_.win, k, R, phi[(n - 1) % 3],
-                                    n >= 2 ? phi[(n - 2) % 3] : nullptr,
+        launched(rp::launch_step<T>(S_, sys_.size() == 1 ? &ham1_ : nullptr, aniso_, d_fdev_,
+                                    rows_.field, rows_.win, k, R,
+                                    phi[(n - 1) % 3], n >= 2 ? phi[(n - 2) % 3] : nullptr,
                                     mode == rp::MODE_LAST ? nullptr : phi[n % 3], Q, X_, d_coef_,
                                     n_c_, n, mode, st_),
                  "step kernel");
         step_launches++;
-        bytes += (mode == rp::MODE_FIRST ? 3.5 : (mode == rp::MODE_MID ? 5.25 : 4.25)) * vbytes * (double)act;
+        bytes += (mode == rp::MODE_FIRST ? 3.5 : (mode == rp::MODE_MID ? 5.25 : 4.25)) * vbytes;
       }
       if (o_.profile) {
         ck(cudaEventRecord(pev.back(), st_), "cudaEventRecord");
@@ -309,7 +349,7 @@ class YieldEngine {
       }
       step_bytes_all += bytes;
       row_terms += act * (long long)n_c_;
-      launched(rp::launch_gram_integrate<T>(X_, d_W_, rows_.field, rows_.win, k, R, hs_.Z, n_c_,
+      launched(rp::launch_gram_integrate<T>(S_, X_, d_W_, rows_.field, rows_.win, k, R, n_c_,
                                             rows_.integral, st_),
                "gram-integral kernel");
       // rows whose window ends after this macro-step: finish and refill
@@ -321,8 +361,8 @@ class YieldEngine {
       if (!any) continue;
       ck(cudaMemcpyAsync(rows_.flag, h_flag.data(), R * sizeof(int), cudaMemcpyHostToDevice, st_), "h2d flags");
       h2d += (long long)R * sizeof(int);
-      launched(rp::launch_norm<T>(S0_, S1_, rows_.win, rows_.flag, R, hs_.Z, rows_.survival, st_), "norm kernel");
-      launched(rp::launch_finalize(rows_, R, hs_.k_S, d_ps, st_), "finalize kernel");
+      launched(rp::launch_norm<T>(S_, S0_, S1_, rows_.win, rows_.flag, R, rows_.survival, st_), "norm kernel");
+      launched(rp::launch_finalize<T>(S_, rows_, R, d_ps, st_), "finalize kernel");
       bool refill = false;
       for (int r = 0; r < R; ++r) {
         if (!h_flag[r]) continue;
@@ -348,13 +388,20 @@ class YieldEngine {
     ck(e, what);
     launches++;
   }
-  const rp::HostSystem& hs_;
+  std::vector<const rp::HostSystem*> sys_;
   const rp_options& o_;
   int n_c_;
   cudaStream_t st_;
   Arena& ar_;
-  rp::HamDev<T> H_;
-  rp::LayoutDev L_;
+  long long Zslot_ = 1;
+  int aniso_ = 0;
+  rp::HamDev<T>* d_ham_ = nullptr;
+  rp::LayoutDev* d_lay_ = nullptr;
+  double* d_kS_ = nullptr;
+  int* row_sys_ = nullptr;
+  uint32_t* d_pair_ = nullptr;
+  rp::HamDev<T> ham1_{};
+  rp::SysTab<T> S_{};
   uint64_t seed_ = 0;
   int R_ = 0;
   rp::FieldDev<T>* d_fdev_ = nullptr;
@@ -380,7 +427,8 @@ int choose_rows(const rp::HostSystem& hs, const rp_options& o, int n_c, long lon
 
 std::vector<Item> make_items(const std::vector<rp::FieldPlan>& plans, const std::vector<long long>& first,
                              const std::vector<long long>& count, const std::vector<long long>& out0,
-                             long long sample_offset, bool deterministic) {
+                             long long sample_offset, bool deterministic,
+                             const std::vector<int>* sys_of_field = nullptr) {
   // most expensive fields first, so that rows finish in waves
   std::vector<int> forder(plans.size());
   for (size_t f = 0; f < plans.size(); ++f) forder[f] = (int)f;
@@ -390,7 +438,7 @@ std::vector<Item> make_items(const std::vector<rp::FieldPlan>& plans, const std:
   for (int f : forder)
     for (long long s = first[f]; s < first[f] + count[f]; ++s)
       items.push_back(Item{f, deterministic ? s : sample_offset + s, out0[f] + (s - first[f]),
-                           (int)plans[f].n_macro});
+                           (int)plans[f].n_macro, sys_of_field ? (*sys_of_field)[f] : 0});
   return items;
 }
 
@@ -471,7 +519,7 @@ rp_status run_yields(rp_system* sys, int n_fields, const double* fields, int M, 
   long long d2h = 0;
   {
     Arena ar(st);
-    YieldEngine<T> eng(hs, o, n_c, st, ar);
+    YieldEngine<T> eng({&hs}, o, n_c, st, ar);
     eng.set_seed(seed);
     ck(cudaEventRecord(ev.a, st), "cudaEventRecord");
     eng.set_fields(plans);
@@ -527,7 +575,7 @@ rp_status run_converged(rp_system* sys, int n_fields, const double* fields, doub
   int R = 0;
   {
     Arena ar(st);
-    YieldEngine<T> eng(hs, o, n_c, st, ar);
+    YieldEngine<T> eng({&hs}, o, n_c, st, ar);
     eng.set_seed(seed);
     ck(cudaEventRecord(ev.a, st), "cudaEventRecord");
     eng.set_fields(plans);
@@ -570,7 +618,8 @@ rp_status run_converged(rp_system* sys, int n_fields, const double* fields, doub
           continue;
         }
         const long long need = (long long)std::ceil(1.15 * var / (se_target * se_target)) + 1;
-        want[f] = std::min<long long>(M_max, std::max<long long>(need, m + 1));
+        // at most 4x per round: the spread of few samples is itself uncertain
+        want[f] = std::min<long long>({M_max, std::max<long long>(need, m + 1), 4 * m});
         more = true;
       }
       if (!more) break;
@@ -603,6 +652,407 @@ rp_status run_converged(rp_system* sys, int n_fields, const double* fields, doub
     fill_stats(stats, eng, total_items, R, n_c, ev.a, ev.b, o.profile != 0, d2h);
   }
   ck(cudaStreamSynchronize(st), "free");
+  return RP_OK;
+}
+
+// Converged curve with the learned control variate (see rp_yields_cv in rp.h).
+template <typename T>
+rp_status run_converged_cv(rp_system* sys, int n_fields, const double* fields, double se_target,
+                           int M_min, int M_max, uint64_t seed, double t_max, const rp_options& o,
+                           const rp_cv_plan& cp, double* out, int* M_plain, int* M_cv,
+                           rp_stats* stats) {
+  const rp::HostSystem& hs = sys->hs;
+  cudaStream_t st = (cudaStream_t)o.stream;
+  const int n_c = o.n_cheb > 0 ? o.n_cheb : default_ncheb(o.precision);
+  const double tol = o.tol > 0 ? o.tol : default_tol(o.precision);
+  if (n_c % 4 != 0 || n_c < 8 || n_c > 88)
+    return fail(RP_EINVAL, "n_cheb must be a multiple of 4 in [8, 88]");
+  std::vector<rp::FieldPlan> plans;
+  rp_status ps = plan_all(hs, n_fields, fields, t_max, n_c, tol, plans);
+  if (ps != RP_OK) return ps;
+  // control-variate samples live far above every plain sample index
+  const long long kCvBase = 1LL << 40;
+  const double se2 = se_target * se_target;
+  std::vector<std::vector<double>> pl(n_fields), cvs(n_fields), cvg(n_fields);
+  std::vector<long long> have(n_fields, 0), want(n_fields, M_min), have_cv(n_fields, 0);
+  std::vector<char> is_cv(n_fields, 0);
+  EventPair ev;
+  long long d2h = 0, total_items = 0;
+  int R = 0;
+  rp_cv* cv = nullptr;
+  struct CvGuard {
+    rp_cv** p;
+    ~CvGuard() {
+      if (*p) rp_cv_destroy(*p);
+    }
+  } cvguard{&cv};
+  auto plain_stats = [&](int f, double* mean, double* var) {
+    const long long m = have[f];
+    double a = 0.0, v = 0.0;
+    for (long long i = 0; i < m; ++i) a += pl[f][3 * i];
+    a /= (double)m;
+    for (long long i = 0; i < m; ++i) v += (pl[f][3 * i] - a) * (pl[f][3 * i] - a);
+    *mean = a;
+    *var = v / (double)std::max<long long>(m - 1, 1);
+  };
+  {
+    Arena ar(st);
+    YieldEngine<T> eng({&hs}, o, n_c, st, ar);
+    eng.set_seed(seed);
+    ck(cudaEventRecord(ev.a, st), "cudaEventRecord");
+    eng.set_fields(plans);
+    R = choose_rows<T>(hs, o, n_c, std::max<long long>((long long)n_fields * M_min, 256));
+    eng.alloc_rows(R);
+    // run counts[f] new samples of field f starting at first[f]; per-sample results appended
+    auto run_round = [&](const std::vector<long long>& first, const std::vector<long long>& count,
+                         std::vector<std::vector<double>>& dst) {
+      std::vector<long long> out0(n_fields);
+      long long n = 0;
+      for (int f = 0; f < n_fields; ++f) {
+        out0[f] = n;
+        n += count[f];
+      }
+      if (n == 0) return;
+      const std::vector<Item> items = make_items(plans, first, count, out0, 0, false);
+      double* d_ps = ar.get<double>((size_t)n * 3);
+      eng.run(items, d_ps);
+      std::vector<double> h((size_t)n * 3);
+      ck(cudaMemcpyAsync(h.data(), d_ps, h.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "d2h round");
+      ck(cudaStreamSynchronize(st), "round");
+      d2h += (long long)h.size() * sizeof(double);
+      total_items += n;
+      for (int f = 0; f < n_fields; ++f)
+        dst[f].insert(dst[f].end(), h.begin() + out0[f] * 3, h.begin() + (out0[f] + count[f]) * 3);
+    };
+    // 1. plain pilot, then plain rounds for fields below the control-variate threshold and
+    //    plain training samples for the others
+    for (int round = 0; round < 8; ++round) {
+      std::vector<long long> first(n_fields), count(n_fields);
+      long long n = 0;
+      for (int f = 0; f < n_fields; ++f) {
+        first[f] = o.sample_offset + have[f];
+        count[f] = std::max<long long>(0, want[f] - have[f]);
+        n += count[f];
+      }
+      if (n == 0) break;
+      run_round(first, count, pl);
+      for (int f = 0; f < n_fields; ++f) have[f] += count[f];
+      bool more = false;
+      for (int f = 0; f < n_fields; ++f) {
+        double mean, var;
+        plain_stats(f, &mean, &var);
+        const long long need = (long long)std::ceil(1.15 * var / se2) + 1;
+        // the control variate pays where the plain estimate would need well
+        // more samples than the training set
+        if (round == 0 && need >= std::max<long long>(cp.cv_threshold, 2LL * cp.M_train)) is_cv[f] = 1;
+        if (is_cv[f]) {
+          want[f] = std::min<long long>({std::max<long long>(have[f], cp.M_train), M_max, 4 * have[f]});
+        } else if (var / (double)have[f] <= se2 || have[f] >= M_max) {
+          want[f] = have[f];
+        } else {
+          want[f] = std::min<long long>({M_max, std::max<long long>(need, have[f] + 1), 4 * have[f]});
+        }
+        more = more || want[f] > have[f];
+      }
+      if (!more) break;
+    }
+    // 2. train on every plain sample of the control-variate fields
+    std::vector<double> tB, tphi;
+    std::vector<long long> ts;
+    for (int f = 0; f < n_fields; ++f)
+      if (is_cv[f])
+        for (long long i = 0; i < have[f]; ++i) {
+          tB.push_back(fields[f]);
+          ts.push_back(o.sample_offset + i);
+          tphi.push_back(pl[f][3 * i]);
+        }
+    std::vector<double> mu(n_fields, 0.0), vmu(n_fields, 0.0);
+    if (tB.size() >= 2) {
+      rp_cv_options net = cp.net;
+      net.stream = o.stream;
+      rp_status cs = rp_cv_create(sys, &net, &cv);
+      if (cs != RP_OK) return cs;
+      cs = rp_cv_train(cv, (int)tB.size(), tB.data(), ts.data(), seed, o.pair_id, tphi.data(), nullptr);
+      if (cs != RP_OK) return cs;
+      std::vector<double> Bcv;
+      std::vector<int> fidx;
+      for (int f = 0; f < n_fields; ++f)
+        if (is_cv[f]) {
+          Bcv.push_back(fields[f]);
+          fidx.push_back(f);
+        }
+      std::vector<double> m(Bcv.size()), vm(Bcv.size());
+      // mu from its own directions (pair word with bit 30 set)
+      cs = rp_cv_mean(cv, (int)Bcv.size(), Bcv.data(), cp.n_mc, seed, o.pair_id ^ 0x40000000u,
+                      m.data(), vm.data());
+      if (cs != RP_OK) return cs;
+      for (size_t i = 0; i < fidx.size(); ++i) {
+        mu[fidx[i]] = m[i];
+        vmu[fidx[i]] = vm[i];
+      }
+    } else {
+      std::fill(is_cv.begin(), is_cv.end(), 0);
+    }
+    // 3. control-variate rounds on fresh samples until the combined SE meets the target
+    std::vector<double> cvout(5 * (size_t)n_fields, 0.0);
+    auto cv_estimates = [&]() {
+      std::vector<long long> off, cnt;
+      std::vector<double> allp, allg;
+      std::vector<int> fidx;
+      for (int f = 0; f < n_fields; ++f)
+        if (is_cv[f] && have_cv[f] >= 2) {
+          off.push_back((long long)allg.size());
+          cnt.push_back(have_cv[f]);
+          allp.insert(allp.end(), cvs[f].begin(), cvs[f].end());
+          allg.insert(allg.end(), cvg[f].begin(), cvg[f].end());
+          fidx.push_back(f);
+        }
+      if (fidx.empty()) return;
+      std::vector<double> m(fidx.size()), vm(fidx.size()), o5(5 * fidx.size());
+      for (size_t i = 0; i < fidx.size(); ++i) {
+        m[i] = mu[fidx[i]];
+        vm[i] = vmu[fidx[i]];
+      }
+      rp_status cs = rp_cv_estimate(cv, (int)fidx.size(), off.data(), cnt.data(), allp.data(),
+                                    allg.data(), m.data(), vm.data(), o5.data());
+      if (cs != RP_OK) throw CudaFail{cs, rp_last_error()};
+      for (size_t i = 0; i < fidx.size(); ++i)
+        for (int q = 0; q < 5; ++q) cvout[5 * fidx[i] + q] = o5[5 * i + q];
+    };
+    std::vector<long long> want_cv(n_fields, 0);
+    for (int f = 0; f < n_fields; ++f)
+      if (is_cv[f]) {
+        double mean, var;
+        plain_stats(f, &mean, &var);
+        const double rem = 1.0 / se2 - (double)have[f] / var;  // precision still missing
+        want_cv[f] = rem > 0 ? std::max<long long>(16, (long long)std::ceil(0.3 * var * rem)) : 0;
+      }
+    for (int round = 0; round < 8; ++round) {
+      std::vector<long long> first(n_fields), count(n_fields);
+      long long n = 0;
+      for (int f = 0; f < n_fields; ++f) {
+        first[f] = kCvBase + o.sample_offset + have_cv[f];
+        count[f] = is_cv[f] ? std::max<long long>(0, want_cv[f] - have_cv[f]) : 0;
+        n += count[f];
+      }
+      if (n == 0) break;
+      std::vector<std::vector<double>> fresh(n_fields);
+      run_round(first, count, fresh);
+      for (int f = 0; f < n_fields; ++f) {
+        if (!count[f]) continue;
+        std::vector<double> Bf(count[f], fields[f]), g(count[f]);
+        std::vector<long long> sf(count[f]);
+        for (long long i = 0; i < count[f]; ++i) sf[i] = first[f] + i;
+        rp_status cs = rp_cv_eval(cv, (int)count[f], Bf.data(), sf.data(), seed, o.pair_id, g.data());
+        if (cs != RP_OK) return cs;
+        cvs[f].insert(cvs[f].end(), fresh[f].begin(), fresh[f].end());
+        cvg[f].insert(cvg[f].end(), g.begin(), g.end());
+        have_cv[f] += count[f];
+      }
+      cv_estimates();
+      bool more = false;
+      for (int f = 0; f < n_fields; ++f) {
+        if (!is_cv[f] || have_cv[f] < 2) continue;
+        double mean, var;
+        plain_stats(f, &mean, &var);
+        const double prec = (double)have[f] / var + 1.0 / (cvout[5 * f + 1] * cvout[5 * f + 1]);
+        if (prec >= 1.0 / se2 || have_cv[f] >= M_max) continue;
+        // residual variance per control-variate sample
+        const double vres = cvout[5 * f + 1] * cvout[5 * f + 1] * (double)have_cv[f];
+        const double need = std::ceil(1.15 * vres * (1.0 / se2 - (double)have[f] / var)) + 1;
+        want_cv[f] = std::min<long long>({M_max, std::max<long long>((long long)need, have_cv[f] + 1),
+                                          4 * have_cv[f]});
+        more = true;
+      }
+      if (!more) break;
+    }
+    // 4. plain statistics on the device over every plain sample, then combine
+    long long tot = 0;
+    std::vector<long long> offcnt(2 * (size_t)n_fields);
+    for (int f = 0; f < n_fields; ++f) {
+      offcnt[f] = tot;
+      offcnt[n_fields + f] = have[f];
+      tot += have[f];
+    }
+    std::vector<double> all;
+    all.reserve((size_t)tot * 3);
+    for (int f = 0; f < n_fields; ++f) all.insert(all.end(), pl[f].begin(), pl[f].end());
+    double* d_all = ar.get<double>((size_t)std::max<long long>(tot, 1) * 3);
+    long long* d_off = ar.get<long long>(2 * (size_t)n_fields);
+    double* d_stats = ar.get<double>((size_t)n_fields * 5);
+    ck(cudaMemcpyAsync(d_all, all.data(), all.size() * sizeof(double), cudaMemcpyHostToDevice, st), "h2d");
+    ck(cudaMemcpyAsync(d_off, offcnt.data(), offcnt.size() * sizeof(long long), cudaMemcpyHostToDevice, st), "h2d");
+    eng.h2d += (long long)(all.size() * sizeof(double) + offcnt.size() * sizeof(long long));
+    ck(rp::launch_stats(d_all, d_off, d_off + n_fields, n_fields, d_stats, st), "stats kernel");
+    eng.launches++;
+    std::vector<double> pst((size_t)n_fields * 5);
+    ck(cudaMemcpyAsync(pst.data(), d_stats, pst.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "d2h stats");
+    d2h += (long long)pst.size() * sizeof(double);
+    ck(cudaEventRecord(ev.b, st), "cudaEventRecord");
+    ck(cudaStreamSynchronize(st), "kernel execution");
+    for (int f = 0; f < n_fields; ++f) {
+      const double mp = pst[5 * f], sp = pst[5 * f + 2];
+      double* of = out + 8 * f;
+      of[2] = mp;
+      of[3] = sp;
+      if (is_cv[f] && have_cv[f] >= 2) {
+        const double mc = cvout[5 * f], sc = cvout[5 * f + 1];
+        const double wp = sp > 0 ? 1.0 / (sp * sp) : 0.0, wc = sc > 0 ? 1.0 / (sc * sc) : 0.0;
+        of[0] = (wp + wc) > 0 ? (wp * mp + wc * mc) / (wp + wc) : mp;
+        of[1] = (wp + wc) > 0 ? 1.0 / std::sqrt(wp + wc) : sp;
+        of[4] = mc;
+        of[5] = sc;
+        of[6] = cvout[5 * f + 4];
+        of[7] = 1.0;
+      } else {
+        of[0] = mp;
+        of[1] = sp;
+        of[4] = of[5] = of[6] = of[7] = 0.0;
+      }
+      if (M_plain) M_plain[f] = (int)have[f];
+      if (M_cv) M_cv[f] = (int)have_cv[f];
+    }
+    fill_stats(stats, eng, total_items, R, n_c, ev.a, ev.b, o.profile != 0, d2h);
+  }
+  ck(cudaStreamSynchronize(st), "free");
+  return RP_OK;
+}
+
+// Several radical pairs in one pass (see rp_yields_batch in rp.h): systems are
+// grouped by size so that a row slot is at most twice a system's Z; every
+// group runs all its (system, field, sample) items on one pool of rows.
+template <typename T>
+rp_status run_batch(int n_sys, rp_system* const* systems, const int* n_fields,
+                    const double* const* fields, const int* M, const double* t_max, uint64_t seed,
+                    const rp_options& o, double* const* out, rp_stats* stats) {
+  cudaStream_t st = (cudaStream_t)o.stream;
+  const int n_c = o.n_cheb > 0 ? o.n_cheb : default_ncheb(o.precision);
+  const double tol = o.tol > 0 ? o.tol : default_tol(o.precision);
+  if (n_c % 4 != 0 || n_c < 8 || n_c > 88)
+    return fail(RP_EINVAL, "n_cheb must be a multiple of 4 in [8, 88]");
+  // plans and per-sample output offsets of every (system, field)
+  std::vector<std::vector<rp::FieldPlan>> plans(n_sys);
+  std::vector<long long> base(n_sys + 1, 0);
+  long long n_pairs = 0;
+  for (int s = 0; s < n_sys; ++s) {
+    rp_status ps = plan_all(systems[s]->hs, n_fields[s], fields[s], t_max[s], n_c, tol, plans[s]);
+    if (ps != RP_OK) return fail(ps, "system " + std::to_string(s) + ": " + rp_last_error());
+    base[s + 1] = base[s] + (long long)n_fields[s] * M[s];
+    n_pairs += n_fields[s];
+  }
+  const long long n_samples = base[n_sys];
+  // groups by ceil(log2 Z), largest first
+  std::vector<int> order(n_sys);
+  for (int s = 0; s < n_sys; ++s) order[s] = s;
+  auto lg = [&](int s) {
+    int b = 0;
+    while ((1LL << b) < systems[s]->hs.Z) ++b;
+    return b;
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lg(a) > lg(b); });
+  EventPair ev;
+  long long launches = 0, step_launches = 0, row_terms = 0, h2d = 0, d2h = 0;
+  double step_bytes = 0.0, step_ms = 0.0;
+  long long step_timed = 0;
+  int R_max = 0;
+  Arena outer(st);
+  double* d_ps = outer.get<double>((size_t)std::max<long long>(n_samples, 1) * 3);
+  ck(cudaEventRecord(ev.a, st), "cudaEventRecord");
+  for (size_t g0 = 0; g0 < order.size();) {
+    size_t g1 = g0;
+    while (g1 < order.size() && lg(order[g1]) == lg(order[g0])) ++g1;
+    std::vector<const rp::HostSystem*> group;
+    std::vector<uint32_t> pairs;
+    std::vector<rp::FieldPlan> gplans;
+    std::vector<int> sys_of_field;
+    std::vector<long long> first, count, out0;
+    for (size_t i = g0; i < g1; ++i) {
+      const int s = order[i];
+      const int gs = (int)group.size();
+      group.push_back(&systems[s]->hs);
+      pairs.push_back(o.pair_id + (uint32_t)s);
+      for (int f = 0; f < n_fields[s]; ++f) {
+        gplans.push_back(plans[s][f]);
+        sys_of_field.push_back(gs);
+        first.push_back(0);
+        count.push_back(M[s]);
+        out0.push_back(base[s] + (long long)f * M[s]);
+      }
+    }
+    const std::vector<Item> items = make_items(gplans, first, count, out0, o.sample_offset, false,
+                                               &sys_of_field);
+    {
+      Arena ar(st);
+      YieldEngine<T> eng(group, o, n_c, st, ar, &pairs);
+      eng.set_seed(seed);
+      eng.set_fields(gplans);
+      long long Zmax = 1;
+      for (auto* h : group) Zmax = std::max<long long>(Zmax, h->Z);
+      rp::HostSystem probe;
+      probe.Z = Zmax;
+      const int R = choose_rows<T>(probe, o, n_c, (long long)items.size());
+      R_max = std::max(R_max, R);
+      eng.alloc_rows(R);
+      eng.run(items, d_ps);
+      ck(cudaStreamSynchronize(st), "group");
+      launches += eng.launches;
+      step_launches += eng.step_launches;
+      row_terms += eng.row_terms;
+      h2d += eng.h2d;
+      step_bytes += eng.step_bytes_all;
+      for (size_t i = 0; i + 1 < eng.pev.size(); i += 2) {
+        float t = 0.f;
+        ck(cudaEventElapsedTime(&t, eng.pev[i], eng.pev[i + 1]), "cudaEventElapsedTime");
+        step_ms += t;
+        step_timed += eng.pev_launches[i / 2];
+      }
+    }
+    g0 = g1;
+  }
+  // per-(system, field) statistics on the device
+  std::vector<long long> offcnt(2 * (size_t)n_pairs);
+  {
+    long long q = 0;
+    for (int s = 0; s < n_sys; ++s)
+      for (int f = 0; f < n_fields[s]; ++f, ++q) {
+        offcnt[q] = base[s] + (long long)f * M[s];
+        offcnt[n_pairs + q] = M[s];
+      }
+  }
+  long long* d_off = outer.get<long long>(2 * (size_t)n_pairs);
+  double* d_stats = outer.get<double>(5 * (size_t)n_pairs);
+  ck(cudaMemcpyAsync(d_off, offcnt.data(), offcnt.size() * sizeof(long long), cudaMemcpyHostToDevice, st), "h2d");
+  h2d += (long long)(offcnt.size() * sizeof(long long));
+  ck(rp::launch_stats(d_ps, d_off, d_off + n_pairs, (int)n_pairs, d_stats, st), "stats kernel");
+  ++launches;
+  std::vector<double> hst(5 * (size_t)n_pairs);
+  ck(cudaMemcpyAsync(hst.data(), d_stats, hst.size() * sizeof(double), cudaMemcpyDeviceToHost, st), "d2h");
+  d2h += (long long)(hst.size() * sizeof(double));
+  ck(cudaEventRecord(ev.b, st), "cudaEventRecord");
+  ck(cudaStreamSynchronize(st), "batch");
+  {
+    long long q = 0;
+    for (int s = 0; s < n_sys; ++s)
+      for (int f = 0; f < n_fields[s]; ++f, ++q)
+        for (int c = 0; c < 5; ++c) out[s][5 * f + c] = hst[5 * q + c];
+  }
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->kernel_launches = launches;
+    stats->step_launches = step_launches;
+    stats->row_terms = row_terms;
+    stats->propagations = n_samples;
+    stats->rows = R_max;
+    stats->n_cheb = n_c;
+    float ms = 0.f;
+    ck(cudaEventElapsedTime(&ms, ev.a, ev.b), "cudaEventElapsedTime");
+    stats->device_ms = ms;
+    stats->step_ms = step_ms;
+    stats->step_bytes = step_bytes;
+    stats->step_launches_timed = step_timed;
+    stats->h2d_bytes = h2d;
+    stats->d2h_bytes = d2h;
+  }
   return RP_OK;
 }
 
@@ -820,6 +1270,96 @@ rp_status rp_yields_converged(rp_system* s, int n_fields, const double* fields, 
   }
 }
 
+void rp_cv_default_plan(rp_cv_plan* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->M_train = 300;
+  p->cv_threshold = 150;
+  p->n_mc = 1LL << 18;
+  rp_cv_default_options(&p->net);
+}
+
+rp_status rp_yields_cv(rp_system* s, int n_fields, const double* fields, double se_target,
+                       int M_min, int M_max, uint64_t seed, double t_max, const rp_options* opt,
+                       const rp_cv_plan* plan, double* out, int* M_plain, int* M_cv,
+                       rp_stats* stats) {
+  g_err.clear();
+  rp_options o;
+  if (opt) o = *opt;
+  else rp_default_options(&o);
+  rp_cv_plan cp;
+  if (plan) cp = *plan;
+  else rp_cv_default_plan(&cp);
+  if (!s) return fail(RP_EINVAL, "system is NULL");
+  if (n_fields < 0) return fail(RP_EINVAL, "n_fields must be >= 0");
+  if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
+  if (o.deterministic) return fail(RP_EINVAL, "rp_yields_cv samples coherent states only");
+  if (!(se_target > 0.0) || !std::isfinite(se_target)) return fail(RP_EINVAL, "se_target must be positive");
+  if (M_min < 2 || M_max < M_min) return fail(RP_EINVAL, "need 2 <= M_min <= M_max");
+  if (cp.M_train < 2 || cp.cv_threshold < 2 || cp.n_mc < 2) return fail(RP_EINVAL, "bad control-variate plan");
+  if (!(t_max > 0.0) || !std::isfinite(t_max)) return fail(RP_EINVAL, "t_max must be positive and finite");
+  if (o.sample_offset < 0 || o.sample_offset >= (1LL << 39)) return fail(RP_EINVAL, "sample_offset must be in [0, 2^39)");
+  if (n_fields > 0 && (!fields || !out)) return fail(RP_EINVAL, "NULL fields or out");
+  for (int f = 0; f < n_fields; ++f)
+    if (!std::isfinite(fields[f])) return fail(RP_EINVAL, "non-finite field");
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  if (n_fields == 0) return RP_OK;
+  rp_status ds = check_device();
+  if (ds != RP_OK) return ds;
+  try {
+    if (o.precision == RP_FP64)
+      return run_converged_cv<double>(s, n_fields, fields, se_target, M_min, M_max, seed, t_max, o,
+                                      cp, out, M_plain, M_cv, stats);
+    return run_converged_cv<float>(s, n_fields, fields, se_target, M_min, M_max, seed, t_max, o, cp,
+                                   out, M_plain, M_cv, stats);
+  } catch (const CudaFail& e) {
+    return fail(e.st, e.msg);
+  } catch (const std::bad_alloc&) {
+    return fail(RP_ENOMEM, "host allocation failed");
+  }
+}
+
+rp_status rp_yields_batch(int n_sys, rp_system* const* systems, const int* n_fields,
+                          const double* const* fields, const int* M, const double* t_max,
+                          uint64_t seed, const rp_options* opt, double* const* out,
+                          rp_stats* stats) {
+  g_err.clear();
+  rp_options o;
+  if (opt) o = *opt;
+  else rp_default_options(&o);
+  if (n_sys < 0) return fail(RP_EINVAL, "n_sys must be >= 0");
+  if (stats) std::memset(stats, 0, sizeof(*stats));
+  if (n_sys == 0) return RP_OK;
+  if (!systems || !n_fields || !fields || !M || !t_max || !out) return fail(RP_EINVAL, "NULL argument");
+  if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
+  if (o.deterministic) return fail(RP_EINVAL, "rp_yields_batch samples coherent states only");
+  if (o.sample_offset < 0) return fail(RP_EINVAL, "sample_offset must be >= 0");
+  long long total = 0;
+  for (int s = 0; s < n_sys; ++s) {
+    const std::string w = "system " + std::to_string(s) + ": ";
+    if (!systems[s]) return fail(RP_EINVAL, w + "NULL system");
+    if (n_fields[s] < 0) return fail(RP_EINVAL, w + "n_fields must be >= 0");
+    if (n_fields[s] > 0 && (!fields[s] || !out[s])) return fail(RP_EINVAL, w + "NULL fields or out");
+    if (M[s] < 2) return fail(RP_EINVAL, w + "M must be >= 2");
+    if (!(t_max[s] > 0.0) || !std::isfinite(t_max[s])) return fail(RP_EINVAL, w + "t_max must be positive and finite");
+    for (int f = 0; f < n_fields[s]; ++f)
+      if (!std::isfinite(fields[s][f])) return fail(RP_EINVAL, w + "non-finite field");
+    total += (long long)n_fields[s] * M[s];
+  }
+  if (total == 0) return RP_OK;
+  rp_status ds = check_device();
+  if (ds != RP_OK) return ds;
+  try {
+    if (o.precision == RP_FP64)
+      return run_batch<double>(n_sys, systems, n_fields, fields, M, t_max, seed, o, out, stats);
+    return run_batch<float>(n_sys, systems, n_fields, fields, M, t_max, seed, o, out, stats);
+  } catch (const CudaFail& e) {
+    return fail(e.st, e.msg);
+  } catch (const std::bad_alloc&) {
+    return fail(RP_ENOMEM, "host allocation failed");
+  }
+}
+
 rp_status rp_apply_h(rp_system* s, double B, int precision, int n_vec, const void* x, void* y,
                      void* stream) {
   g_err.clear();
@@ -838,18 +1378,26 @@ rp_status rp_apply_h(rp_system* s, double B, int precision, int n_vec, const voi
     const double kbar = 0.5 * (hs.k_S + hs.k_T);
     if (precision == RP_FP64) {
       rp::FieldDev<double> F{rp::kGammaE * B, 1.0, 0.0, 0.5 * kbar};
+      const rp::HamDev<double> H = make_ham<double>(hs);
       auto* d = ar.get<rp::FieldDev<double>>(1);
+      auto* dh = ar.get<rp::HamDev<double>>(1);
       ck(cudaMemcpyAsync(d, &F, sizeof(F), cudaMemcpyHostToDevice, st), "h2d");
-      ck(rp::launch_step<double>(make_ham<double>(hs), d, nullptr, nullptr, 0, n_vec,
-                                 (const double*)x, nullptr, (double*)y, nullptr, nullptr, nullptr,
-                                 0, 0, rp::MODE_APPLY, st), "apply kernel");
+      ck(cudaMemcpyAsync(dh, &H, sizeof(H), cudaMemcpyHostToDevice, st), "h2d");
+      const rp::SysTab<double> S{dh, nullptr, nullptr, nullptr, hs.Z, 0, nullptr};
+      ck(rp::launch_step<double>(S, &H, H.aniso, d, nullptr, nullptr, 0, n_vec, (const double*)x,
+                                 nullptr, (double*)y, nullptr, nullptr, nullptr, 0, 0,
+                                 rp::MODE_APPLY, st), "apply kernel");
     } else {
       rp::FieldDev<float> F{(float)(rp::kGammaE * B), 1.f, 0.f, (float)(0.5 * kbar)};
+      const rp::HamDev<float> H = make_ham<float>(hs);
       auto* d = ar.get<rp::FieldDev<float>>(1);
+      auto* dh = ar.get<rp::HamDev<float>>(1);
       ck(cudaMemcpyAsync(d, &F, sizeof(F), cudaMemcpyHostToDevice, st), "h2d");
-      ck(rp::launch_step<float>(make_ham<float>(hs), d, nullptr, nullptr, 0, n_vec,
-                                (const float*)x, nullptr, (float*)y, nullptr, nullptr, nullptr, 0,
-                                0, rp::MODE_APPLY, st), "apply kernel");
+      ck(cudaMemcpyAsync(dh, &H, sizeof(H), cudaMemcpyHostToDevice, st), "h2d");
+      const rp::SysTab<float> S{dh, nullptr, nullptr, nullptr, hs.Z, 0, nullptr};
+      ck(rp::launch_step<float>(S, &H, H.aniso, d, nullptr, nullptr, 0, n_vec, (const float*)x, nullptr,
+                                (float*)y, nullptr, nullptr, nullptr, 0, 0, rp::MODE_APPLY, st),
+         "apply kernel");
     }
     ck(cudaStreamSynchronize(st), "apply kernel execution");
   } catch (const CudaFail& e) {
@@ -880,13 +1428,19 @@ rp_status rp_init_states(rp_system* s, int precision, uint64_t seed, uint32_t pa
     double* uv = angles ? ar.get<double>((size_t)n * std::max(hs.n_nuc, 1) * 2) : nullptr;
     ck(cudaMemcpyAsync(d_s, smp.data(), n * sizeof(long long), cudaMemcpyHostToDevice, st), "h2d");
     const rp::LayoutDev L = make_layout(hs);
-    ck(rp::launch_coherent_amps(L, d_s, nullptr, n, seed, pair_id, amps, uv, st), "coherent amplitudes");
-    if (precision == RP_FP64)
-      ck(rp::launch_init_state<double>(L, amps, d_s, nullptr, nullptr, n, 0, (double*)psi,
+    auto* dl = ar.get<rp::LayoutDev>(1);
+    ck(cudaMemcpyAsync(dl, &L, sizeof(L), cudaMemcpyHostToDevice, st), "h2d");
+    if (precision == RP_FP64) {
+      const rp::SysTab<double> S{nullptr, dl, nullptr, nullptr, hs.Z, pair_id, nullptr};
+      ck(rp::launch_coherent_amps<double>(S, d_s, nullptr, n, seed, amps, uv, st), "coherent amplitudes");
+      ck(rp::launch_init_state<double>(S, amps, d_s, nullptr, nullptr, n, 0, (double*)psi,
                                        (double*)psi, nullptr, nullptr, st), "initial states");
-    else
-      ck(rp::launch_init_state<float>(L, amps, d_s, nullptr, nullptr, n, 0, (float*)psi,
+    } else {
+      const rp::SysTab<float> S{nullptr, dl, nullptr, nullptr, hs.Z, pair_id, nullptr};
+      ck(rp::launch_coherent_amps<float>(S, d_s, nullptr, n, seed, amps, uv, st), "coherent amplitudes");
+      ck(rp::launch_init_state<float>(S, amps, d_s, nullptr, nullptr, n, 0, (float*)psi,
                                       (float*)psi, nullptr, nullptr, st), "initial states");
+    }
     if (angles && hs.n_nuc > 0)
       ck(cudaMemcpyAsync(angles, uv, (size_t)n * hs.n_nuc * 2 * sizeof(double), cudaMemcpyDeviceToHost, st), "d2h");
     ck(cudaStreamSynchronize(st), "init kernels");

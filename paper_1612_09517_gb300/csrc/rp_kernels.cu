@@ -2,6 +2,8 @@
 // coherent-state sampling (Eqs. 15, 17-19), matrix-free H.psi fused with the
 // Chebyshev recurrence (Eqs. 1-4, 13), the singlet Gram / exact time integral
 // (Eqs. 20, 22) and the per-field averages with standard errors (Eqs. 18, 23).
+#include <cstring>
+
 #include "rp_kernels.cuh"
 
 namespace rp {
@@ -252,16 +254,24 @@ __device__ __forceinline__ void half_nucleus(Cx<T> (&y)[4], T (&b1)[3], T (&b2)[
   }
 }
 
+// Body of one Chebyshev term; H is either the kernel-parameter copy (one
+// system per launch) or a shared-memory copy of the row's system.
 template <typename T, bool ANISO>
+__device__ __forceinline__ void step_body(const HamDev<T>& H, const SysTab<T>& S, Cx<T>* tile,
+                                          const FieldDev<T>* __restrict__ fields, int f, int r,
+                                          const T* __restrict__ cur, const T* __restrict__ prev,
+                                          T* __restrict__ next, T* __restrict__ acc,
+                                          T* __restrict__ X, const T* __restrict__ coef, int n_c,
+                                          int n, int mode);
+
+template <typename T, bool ANISO, bool MULTI>
 __global__ void __launch_bounds__(kStepThreads, sizeof(T) == 4 ? 4 : 2) k_cheb_step(
-    const HamDev<T> H, const FieldDev<T>* __restrict__ fields, const int* __restrict__ row_field,
-    const int2* __restrict__ row_win, int macro, const T* __restrict__ cur,
-    const T* __restrict__ prev, T* __restrict__ next, T* __restrict__ acc, T* __restrict__ X,
-    const T* __restrict__ coef, int n_c, int n, int mode, int n_in) {
+    const SysTab<T> S, const HamDev<T> H1, const FieldDev<T>* __restrict__ fields,
+    const int* __restrict__ row_field, const int2* __restrict__ row_win, int macro,
+    const T* __restrict__ cur, const T* __restrict__ prev, T* __restrict__ next,
+    T* __restrict__ acc, T* __restrict__ X, const T* __restrict__ coef, int n_c, int n, int mode) {
   extern __shared__ __align__(16) unsigned char step_smem[];
   Cx<T>* tile = reinterpret_cast<Cx<T>*>(step_smem);  // planes x blockDim x 16 B
-  const unsigned Z = (unsigned)H.Z;
-  const unsigned m = blockIdx.x * blockDim.x + threadIdx.x;
   const int r = blockIdx.y;
   int f = 0;
   if (mode != MODE_APPLY) {
@@ -269,9 +279,34 @@ __global__ void __launch_bounds__(kStepThreads, sizeof(T) == 4 ? 4 : 2) k_cheb_s
     if (macro < w.x || macro >= w.y) return;  // the whole block: one row
     f = row_field[r];
   }
+  if (MULTI) {
+    __shared__ HamDev<T> Hs;  // constants of this row's system
+    const int sidx = S.row_sys ? S.row_sys[r] : 0;
+    const int4* src = reinterpret_cast<const int4*>(S.ham + sidx);
+    int4* dst = reinterpret_cast<int4*>(&Hs);
+    for (int i = threadIdx.x; i < (int)(sizeof(HamDev<T>) / 16); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    step_body<T, ANISO>(Hs, S, tile, fields, f, r, cur, prev, next, acc, X, coef, n_c, n, mode);
+  } else {
+    step_body<T, ANISO>(H1, S, tile, fields, f, r, cur, prev, next, acc, X, coef, n_c, n, mode);
+  }
+}
+
+template <typename T, bool ANISO>
+__device__ __forceinline__ void step_body(const HamDev<T>& H, const SysTab<T>& S, Cx<T>* tile,
+                                          const FieldDev<T>* __restrict__ fields, int f, int r,
+                                          const T* __restrict__ cur, const T* __restrict__ prev,
+                                          T* __restrict__ next, T* __restrict__ acc,
+                                          T* __restrict__ X, const T* __restrict__ coef, int n_c,
+                                          int n, int mode) {
+  const unsigned Z = (unsigned)H.Z;
+  const unsigned m = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = m < Z;
-  const size_t row0 = (size_t)r * Z * 8;
+  const size_t row0 = (size_t)r * S.Zslot * 8;
   const T* c = cur + row0;
+  // spin-1/2 nuclei whose partner m XOR 2^p lies in this (power-of-two) block
+  const int lb = 31 - __clz((int)blockDim.x);
+  const int n_in = H.n_half < lb ? H.n_half : lb;
 
   Cx<T> a[4];
   if (valid) {
@@ -394,7 +429,8 @@ __global__ void __launch_bounds__(kStepThreads, sizeof(T) == 4 ? 4 : 2) k_cheb_s
     return;
   }
   const T* cf = coef + (size_t)f * n_c * 2;
-  T* xr = X + (size_t)r * n_c * Z * 2;
+  const size_t Zs = (size_t)S.Zslot;
+  T* xr = X + (size_t)r * n_c * Zs * 2;
   if (mode == MODE_FIRST) {
     store4(next + off, z);
     const T c0r = cf[0], c0i = cf[1], c1r = cf[2], c1i = cf[3];
@@ -407,7 +443,7 @@ __global__ void __launch_bounds__(kStepThreads, sizeof(T) == 4 ? 4 : 2) k_cheb_s
     }
     store4(acc + off, s);
     store_singlet(xr + (size_t)m * 2, a);
-    store_singlet(xr + ((size_t)Z + m) * 2, z);
+    store_singlet(xr + (Zs + m) * 2, z);
     return;
   }
   Cx<T> pv[4];
@@ -425,7 +461,7 @@ __global__ void __launch_bounds__(kStepThreads, sizeof(T) == 4 ? 4 : 2) k_cheb_s
 #pragma unroll
   for (int e = 0; e < 4; ++e) cmac(s[e], cr, ci, ph[e]);
   store4(acc + off, s);
-  store_singlet(xr + ((size_t)n * Z + m) * 2, ph);
+  store_singlet(xr + ((size_t)n * Zs + m) * 2, ph);
 }
 
 template <int NT>
@@ -452,14 +488,16 @@ constexpr int kGramThreads = 256;
 
 template <typename T>
 __global__ void __launch_bounds__(kGramThreads) k_gram_integrate(
-    const T* __restrict__ X, const double* __restrict__ W, const int* __restrict__ row_field,
-    const int2* __restrict__ row_win, int macro, long long Z, int n_c, int tiles,
-    int groups, int zc, long long z_per_cta, double* __restrict__ integral) {
+    const SysTab<T> S, const T* __restrict__ X, const double* __restrict__ W,
+    const int* __restrict__ row_field, const int2* __restrict__ row_win, int macro, int n_c,
+    int tiles, int groups, int zc, long long z_per_cta, double* __restrict__ integral) {
   const int r = blockIdx.y;
   {
     const int2 w = row_win[r];
     if (macro < w.x || macro >= w.y) return;
   }
+  const long long Z = S.ham[S.row_sys ? S.row_sys[r] : 0].Z;
+  const long long Zs = S.Zslot;
   const long long z0 = (long long)blockIdx.x * z_per_cta;
   const long long z1 = min(Z, z0 + z_per_cta);
   if (z0 >= z1) return;
@@ -488,7 +526,7 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_integrate(
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) a2r[i][j] = a2i[i][j] = T(0);
-  const T* Xr = X + (size_t)r * n_c * Z * 2;
+  const T* Xr = X + (size_t)r * n_c * Zs * 2;
   for (long long c0 = z0; c0 < z1; c0 += zc) {
     __syncthreads();
     for (int idx = tid; idx < n_c * zc; idx += blockDim.x) {
@@ -496,8 +534,8 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_integrate(
       const long long z = c0 + zz;
       Cx<T> v = {T(0), T(0)};
       if (z < z1) {
-        v.re = Xr[((size_t)nn * Z + z) * 2];
-        v.im = Xr[((size_t)nn * Z + z) * 2 + 1];
+        v.re = Xr[((size_t)nn * Zs + z) * 2];
+        v.im = Xr[((size_t)nn * Zs + z) * 2 + 1];
       }
       sx[zz * ldn + nn] = v;
     }
@@ -574,14 +612,16 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_integrate(
 // survival[r] += |psi|^2 over a slice for the flagged rows; psi of a row whose
 // window ended at macro-step e sits in S[e % 2].
 template <typename T>
-__global__ void __launch_bounds__(256) k_norm(const T* __restrict__ S0, const T* __restrict__ S1,
+__global__ void __launch_bounds__(256) k_norm(const SysTab<T> ST, const T* __restrict__ S0,
+                                              const T* __restrict__ S1,
                                               const int2* __restrict__ row_win,
-                                              const int* __restrict__ row_flag, long long Z,
+                                              const int* __restrict__ row_flag,
                                               long long z_per_cta, double* __restrict__ survival) {
   __shared__ double sh[256];
   const int r = blockIdx.y;
   if (row_flag && !row_flag[r]) return;
-  const T* S = ((row_win[r].y & 1) ? S1 : S0) + (size_t)r * Z * 8;
+  const long long Z = ST.ham[ST.row_sys ? ST.row_sys[r] : 0].Z;
+  const T* S = ((row_win[r].y & 1) ? S1 : S0) + (size_t)r * ST.Zslot * 8;
   const long long z0 = (long long)blockIdx.x * z_per_cta;
   const long long z1 = min(Z, z0 + z_per_cta);
   double s = 0.0;
@@ -596,10 +636,11 @@ __global__ void __launch_bounds__(256) k_norm(const T* __restrict__ S0, const T*
   if (threadIdx.x == 0) atomicAdd(survival + r, tot);
 }
 
-__global__ void k_finalize(RowsDev R, int rows, double k_S, double* __restrict__ per_sample) {
+template <typename T>
+__global__ void k_finalize(const SysTab<T> S, RowsDev R, int rows, double* __restrict__ per_sample) {
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= rows || (R.flag && !R.flag[r])) return;
-  const double phiS = k_S * R.integral[r];
+  const double phiS = S.k_S[S.row_sys ? S.row_sys[r] : 0] * R.integral[r];
   const double surv = R.survival[r];
   double* o = per_sample + (size_t)R.out[r] * 3;
   o[0] = phiS;
@@ -679,13 +720,18 @@ __device__ __forceinline__ double u53(uint32_t hi, uint32_t lo) {
 // (cos theta = 1 - 2 u1, phi = 2 pi u2; uniform on the sphere, Eq. 17) and the
 // coherent-state components c_j = sqrt(C(2I, j)) cos^{2I-j}(theta/2)
 // sin^j(theta/2) e^{i j phi}, j = I - M (Eq. 15 expanded in |I, M>).
-__global__ void k_coherent_amps(const LayoutDev L, const long long* __restrict__ row_sample,
+template <typename T>
+__global__ void k_coherent_amps(const SysTab<T> S, const long long* __restrict__ row_sample,
                                 const int* __restrict__ row_flag, int rows, uint64_t seed,
-                                uint32_t pair, double* __restrict__ amps, double* __restrict__ uv) {
+                                double* __restrict__ amps, double* __restrict__ uv) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= rows * L.n_nuc) return;
-  const int r = t / L.n_nuc, p = t % L.n_nuc;
+  if (t >= rows * kMaxNucDev) return;
+  const int r = t / kMaxNucDev, p = t % kMaxNucDev;
   if (row_flag && !row_flag[r]) return;
+  const int sidx = S.row_sys ? S.row_sys[r] : 0;
+  const LayoutDev& L = S.lay[sidx];
+  if (p >= L.n_nuc) return;
+  const uint32_t pair = S.pair_of ? S.pair_of[sidx] : S.pair_base + (uint32_t)sidx;
   const int k = L.input_index[p];
   const unsigned long long s = (unsigned long long)row_sample[r];
   uint32_t c[4] = {(uint32_t)k, (uint32_t)(s & 0xFFFFFFFFull), (uint32_t)(s >> 32), pair};
@@ -715,7 +761,7 @@ __global__ void k_coherent_amps(const LayoutDev L, const long long* __restrict__
 // Flagged rows only (all rows when row_flag is NULL); the state goes to
 // S[start % 2] of the row's window, and the row's integral and survival restart.
 template <typename T>
-__global__ void __launch_bounds__(256) k_init_state(const LayoutDev L,
+__global__ void __launch_bounds__(256) k_init_state(const SysTab<T> S,
                                                     const double* __restrict__ amps,
                                                     const long long* __restrict__ row_sample,
                                                     const int* __restrict__ row_flag,
@@ -730,6 +776,7 @@ __global__ void __launch_bounds__(256) k_init_state(const LayoutDev L,
     integral[r] = 0.0;
     survival[r] = 0.0;
   }
+  const LayoutDev& L = S.lay[S.row_sys ? S.row_sys[r] : 0];
   if (m >= L.Z) return;
   T* psi = (row_win && (row_win[r].x & 1)) ? S1 : S0;
   double pr = 1.0, pi = 0.0;
@@ -754,7 +801,7 @@ __global__ void __launch_bounds__(256) k_init_state(const LayoutDev L,
   v[1] = {(T)(s * pr), (T)(s * pi)};
   v[2] = {(T)(-s * pr), (T)(-s * pi)};
   v[3] = {T(0), T(0)};
-  store4(psi + (size_t)r * L.Z * 8 + (size_t)m * 8, v);
+  store4(psi + (size_t)r * S.Zslot * 8 + (size_t)m * 8, v);
 }
 
 __global__ void k_zero(double* p, size_t n) {
@@ -766,56 +813,65 @@ inline unsigned grid1(long long n, int b) { return (unsigned)((n + b - 1) / b); 
 
 }  // namespace
 
-cudaError_t launch_coherent_amps(const LayoutDev& L, const long long* row_sample,
-                                 const int* row_flag, int rows, uint64_t seed, uint32_t pair,
-                                 double* amps, double* uv, cudaStream_t st) {
-  const long long n = (long long)rows * L.n_nuc;
+template <typename T>
+cudaError_t launch_coherent_amps(const SysTab<T>& S, const long long* row_sample,
+                                 const int* row_flag, int rows, uint64_t seed, double* amps,
+                                 double* uv, cudaStream_t st) {
+  const long long n = (long long)rows * kMaxNucDev;
   if (n == 0) return cudaSuccess;
-  k_coherent_amps<<<grid1(n, 128), 128, 0, st>>>(L, row_sample, row_flag, rows, seed, pair, amps,
-                                                 uv);
+  k_coherent_amps<T><<<grid1(n, 128), 128, 0, st>>>(S, row_sample, row_flag, rows, seed, amps, uv);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_init_state(const LayoutDev& L, const double* amps, const long long* row_sample,
+cudaError_t launch_init_state(const SysTab<T>& S, const double* amps, const long long* row_sample,
                               const int* row_flag, const int2* row_win, int rows,
                               int deterministic, T* S0, T* S1, double* integral, double* survival,
                               cudaStream_t st) {
   if (rows == 0) return cudaSuccess;
-  const int b = L.Z >= 256 ? 256 : (int)((L.Z + 31) / 32 * 32);
-  dim3 grid(grid1(L.Z, b), rows);
-  k_init_state<T><<<grid, b, 0, st>>>(L, amps, row_sample, row_flag, row_win, deterministic, S0,
+  const int b = S.Zslot >= 256 ? 256 : (int)((S.Zslot + 31) / 32 * 32);
+  dim3 grid(grid1(S.Zslot, b), rows);
+  k_init_state<T><<<grid, b, 0, st>>>(S, amps, row_sample, row_flag, row_win, deterministic, S0,
                                       S1, integral, survival);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_step(const HamDev<T>& H, const FieldDev<T>* fields, const int* row_field,
-                        const int2* row_win, int macro, int rows, const T* cur, const T* prev,
-                        T* next, T* acc, T* X, const T* coef, int n_c, int n, int mode,
-                        cudaStream_t st) {
+cudaError_t launch_step(const SysTab<T>& S, const HamDev<T>* one, int aniso,
+                        const FieldDev<T>* fields, const int* row_field, const int2* row_win,
+                        int macro, int rows, const T* cur, const T* prev, T* next, T* acc, T* X,
+                        const T* coef, int n_c, int n, int mode, cudaStream_t st) {
   if (rows == 0) return cudaSuccess;
   // power-of-two blocks so that m XOR 2^p stays inside the block for 2^p < b
   int b = 32;
-  while (b < kStepThreads && b < H.Z) b *= 2;
-  int lb = 0;
-  while ((1 << (lb + 1)) <= b) ++lb;
-  const int n_in = H.n_half < lb ? H.n_half : lb;
+  while (b < kStepThreads && b < S.Zslot) b *= 2;
   const size_t smem = (size_t)b * 4 * sizeof(Cx<T>);
-  dim3 grid(grid1(H.Z, b), rows);
-  if (H.aniso)
-    k_cheb_step<T, true><<<grid, b, smem, st>>>(H, fields, row_field, row_win, macro, cur, prev,
-                                                next, acc, X, coef, n_c, n, mode, n_in);
-  else
-    k_cheb_step<T, false><<<grid, b, smem, st>>>(H, fields, row_field, row_win, macro, cur, prev,
-                                                 next, acc, X, coef, n_c, n, mode, n_in);
+  dim3 grid(grid1(S.Zslot, b), rows);
+  HamDev<T> h1;
+  if (one) h1 = *one;
+  else std::memset(&h1, 0, sizeof(h1));
+  if (one) {
+    if (aniso)
+      k_cheb_step<T, true, false><<<grid, b, smem, st>>>(S, h1, fields, row_field, row_win, macro,
+                                                         cur, prev, next, acc, X, coef, n_c, n, mode);
+    else
+      k_cheb_step<T, false, false><<<grid, b, smem, st>>>(S, h1, fields, row_field, row_win, macro,
+                                                          cur, prev, next, acc, X, coef, n_c, n, mode);
+  } else {
+    if (aniso)
+      k_cheb_step<T, true, true><<<grid, b, smem, st>>>(S, h1, fields, row_field, row_win, macro,
+                                                        cur, prev, next, acc, X, coef, n_c, n, mode);
+    else
+      k_cheb_step<T, false, true><<<grid, b, smem, st>>>(S, h1, fields, row_field, row_win, macro,
+                                                         cur, prev, next, acc, X, coef, n_c, n, mode);
+  }
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_gram_integrate(const T* X, const double* W, const int* row_field,
-                                  const int2* row_win, int macro, int rows, long long Z, int n_c,
-                                  double* integral, cudaStream_t st) {
+cudaError_t launch_gram_integrate(const SysTab<T>& S, const T* X, const double* W,
+                                  const int* row_field, const int2* row_win, int macro, int rows,
+                                  int n_c, double* integral, cudaStream_t st) {
   if (rows == 0) return cudaSuccess;
   const int nt = n_c / 4;
   const int tiles = nt * (nt + 1) / 2;
@@ -831,26 +887,27 @@ cudaError_t launch_gram_integrate(const T* X, const double* W, const int* row_fi
                                          (int)smem);
     if (e != cudaSuccess) return e;
   }
-  dim3 grid((unsigned)((Z + z_per_cta - 1) / z_per_cta), rows);
-  k_gram_integrate<T><<<grid, kGramThreads, smem, st>>>(X, W, row_field, row_win, macro, Z, n_c,
+  dim3 grid((unsigned)((S.Zslot + z_per_cta - 1) / z_per_cta), rows);
+  k_gram_integrate<T><<<grid, kGramThreads, smem, st>>>(S, X, W, row_field, row_win, macro, n_c,
                                                         tiles, groups, zc, z_per_cta, integral);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_norm(const T* S0, const T* S1, const int2* row_win, const int* row_flag,
-                        int rows, long long Z, double* survival, cudaStream_t st) {
+cudaError_t launch_norm(const SysTab<T>& S, const T* S0, const T* S1, const int2* row_win,
+                        const int* row_flag, int rows, double* survival, cudaStream_t st) {
   if (rows == 0) return cudaSuccess;
   long long zper = 256 * 16;
-  dim3 grid(grid1(Z, (int)zper), rows);
-  k_norm<T><<<grid, 256, 0, st>>>(S0, S1, row_win, row_flag, Z, zper, survival);
+  dim3 grid(grid1(S.Zslot, (int)zper), rows);
+  k_norm<T><<<grid, 256, 0, st>>>(S, S0, S1, row_win, row_flag, zper, survival);
   return cudaGetLastError();
 }
 
-cudaError_t launch_finalize(const RowsDev& R, int rows, double k_S, double* per_sample,
+template <typename T>
+cudaError_t launch_finalize(const SysTab<T>& S, const RowsDev& R, int rows, double* per_sample,
                             cudaStream_t st) {
   if (rows == 0) return cudaSuccess;
-  k_finalize<<<grid1(rows, 128), 128, 0, st>>>(R, rows, k_S, per_sample);
+  k_finalize<T><<<grid1(rows, 128), 128, 0, st>>>(S, R, rows, per_sample);
   return cudaGetLastError();
 }
 
@@ -867,28 +924,37 @@ cudaError_t launch_zero(double* p, size_t n, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template cudaError_t launch_init_state<float>(const LayoutDev&, const double*, const long long*,
-                                              const int*, const int2*, int, int, float*, float*,
-                                              double*, double*, cudaStream_t);
-template cudaError_t launch_init_state<double>(const LayoutDev&, const double*, const long long*,
-                                               const int*, const int2*, int, int, double*, double*,
-                                               double*, double*, cudaStream_t);
-template cudaError_t launch_step<float>(const HamDev<float>&, const FieldDev<float>*, const int*,
-                                        const int2*, int, int, const float*, const float*, float*,
-                                        float*, float*, const float*, int, int, int, cudaStream_t);
-template cudaError_t launch_step<double>(const HamDev<double>&, const FieldDev<double>*,
-                                         const int*, const int2*, int, int, const double*,
-                                         const double*, double*, double*, double*, const double*,
-                                         int, int, int, cudaStream_t);
-template cudaError_t launch_gram_integrate<float>(const float*, const double*, const int*,
-                                                  const int2*, int, int, long long, int, double*,
+template cudaError_t launch_coherent_amps<float>(const SysTab<float>&, const long long*, const int*,
+                                                 int, uint64_t, double*, double*, cudaStream_t);
+template cudaError_t launch_init_state<float>(const SysTab<float>&, const double*, const long long*,
+                                              const int*, const int2*, int, int, float*, float*, double*,
+                                              double*, cudaStream_t);
+template cudaError_t launch_step<float>(const SysTab<float>&, const HamDev<float>*, int,
+                                        const FieldDev<float>*, const int*, const int2*, int, int,
+                                        const float*, const float*, float*, float*, float*, const float*, int,
+                                        int, int, cudaStream_t);
+template cudaError_t launch_gram_integrate<float>(const SysTab<float>&, const float*, const double*,
+                                                  const int*, const int2*, int, int, int, double*,
                                                   cudaStream_t);
-template cudaError_t launch_gram_integrate<double>(const double*, const double*, const int*,
-                                                   const int2*, int, int, long long, int, double*,
-                                                   cudaStream_t);
-template cudaError_t launch_norm<float>(const float*, const float*, const int2*, const int*, int,
-                                        long long, double*, cudaStream_t);
-template cudaError_t launch_norm<double>(const double*, const double*, const int2*, const int*,
-                                         int, long long, double*, cudaStream_t);
+template cudaError_t launch_norm<float>(const SysTab<float>&, const float*, const float*, const int2*,
+                                        const int*, int, double*, cudaStream_t);
+template cudaError_t launch_finalize<float>(const SysTab<float>&, const RowsDev&, int, double*,
+                                            cudaStream_t);
+template cudaError_t launch_coherent_amps<double>(const SysTab<double>&, const long long*, const int*,
+                                                 int, uint64_t, double*, double*, cudaStream_t);
+template cudaError_t launch_init_state<double>(const SysTab<double>&, const double*, const long long*,
+                                              const int*, const int2*, int, int, double*, double*, double*,
+                                              double*, cudaStream_t);
+template cudaError_t launch_step<double>(const SysTab<double>&, const HamDev<double>*, int,
+                                        const FieldDev<double>*, const int*, const int2*, int, int,
+                                        const double*, const double*, double*, double*, double*, const double*, int,
+                                        int, int, cudaStream_t);
+template cudaError_t launch_gram_integrate<double>(const SysTab<double>&, const double*, const double*,
+                                                  const int*, const int2*, int, int, int, double*,
+                                                  cudaStream_t);
+template cudaError_t launch_norm<double>(const SysTab<double>&, const double*, const double*, const int2*,
+                                        const int*, int, double*, cudaStream_t);
+template cudaError_t launch_finalize<double>(const SysTab<double>&, const RowsDev&, int, double*,
+                                            cudaStream_t);
 
 }  // namespace rp

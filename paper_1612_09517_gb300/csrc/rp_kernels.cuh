@@ -16,7 +16,7 @@ constexpr int kMaxNucDev = 24;
 // that multiplies I_+ in S.A.I = sum_a S_a (u_a I_+ + conj(u_a) I_- + A_az I_z),
 // stored row-major as (re, im) pairs, and the column (A_xz, A_yz, A_zz).
 template <typename T>
-struct HamDev {
+struct alignas(16) HamDev {
   long long Z;
   int n_nuc, n_half, n_one, aniso;
   T Je;     // 2J S1.S2 coupling J in rad/us
@@ -59,37 +59,58 @@ struct LayoutDev {
   long long stride[kMaxNucDev];
 };
 
+// Systems of one launch: device arrays of per-system constants, the system of
+// each row (NULL: every row is system 0), the slot stride in configurations
+// of the row buffers (>= every system's Z), and the Philox pair word of each
+// system (pair_of[s], or pair_base + s when pair_of is NULL).
+template <typename T>
+struct SysTab {
+  const HamDev<T>* ham;
+  const LayoutDev* lay;
+  const double* k_S;
+  const int* row_sys;
+  long long Zslot;
+  uint32_t pair_base;
+  const uint32_t* pair_of;
+};
+
 // ---- launchers (return cudaGetLastError after the launch) ----
 // row_flag may be NULL (all rows).
 
-cudaError_t launch_coherent_amps(const LayoutDev& L, const long long* row_sample,
-                                 const int* row_flag, int rows, uint64_t seed, uint32_t pair,
-                                 double* amps, double* uv, cudaStream_t st);
+template <typename T>
+cudaError_t launch_coherent_amps(const SysTab<T>& S, const long long* row_sample,
+                                 const int* row_flag, int rows, uint64_t seed, double* amps,
+                                 double* uv, cudaStream_t st);
 
 template <typename T>
-cudaError_t launch_init_state(const LayoutDev& L, const double* amps, const long long* row_sample,
+cudaError_t launch_init_state(const SysTab<T>& S, const double* amps, const long long* row_sample,
                               const int* row_flag, const int2* row_win, int rows,
                               int deterministic, T* S0, T* S1, double* integral, double* survival,
                               cudaStream_t st);
 
+// One Chebyshev term over every row (see k_cheb_step).  one != NULL: every
+// row is that system (its constants travel as kernel parameters); NULL: each
+// row reads its system from S.ham.  aniso selects the anisotropic hyperfine
+// path (needed if any system of the launch has it).
 template <typename T>
-cudaError_t launch_step(const HamDev<T>& H, const FieldDev<T>* fields, const int* row_field,
-                        const int2* row_win, int macro, int rows, const T* cur, const T* prev,
-                        T* next, T* acc, T* X, const T* coef, int n_c, int n, int mode,
-                        cudaStream_t st);
+cudaError_t launch_step(const SysTab<T>& S, const HamDev<T>* one, int aniso,
+                        const FieldDev<T>* fields, const int* row_field, const int2* row_win,
+                        int macro, int rows, const T* cur, const T* prev, T* next, T* acc, T* X,
+                        const T* coef, int n_c, int n, int mode, cudaStream_t st);
 
 // integral[r] += sum_nm W_nm <x_n|x_m> for the macro-step just finished
 // (x_n = singlet slices X[r][n], W per field); one FP64 atomic per CTA.
 template <typename T>
-cudaError_t launch_gram_integrate(const T* X, const double* W, const int* row_field,
-                                  const int2* row_win, int macro, int rows, long long Z, int n_c,
-                                  double* integral, cudaStream_t st);
+cudaError_t launch_gram_integrate(const SysTab<T>& S, const T* X, const double* W,
+                                  const int* row_field, const int2* row_win, int macro, int rows,
+                                  int n_c, double* integral, cudaStream_t st);
 
 template <typename T>
-cudaError_t launch_norm(const T* S0, const T* S1, const int2* row_win, const int* row_flag,
-                        int rows, long long Z, double* survival, cudaStream_t st);
+cudaError_t launch_norm(const SysTab<T>& S, const T* S0, const T* S1, const int2* row_win,
+                        const int* row_flag, int rows, double* survival, cudaStream_t st);
 
-cudaError_t launch_finalize(const RowsDev& R, int rows, double k_S, double* per_sample,
+template <typename T>
+cudaError_t launch_finalize(const SysTab<T>& S, const RowsDev& R, int rows, double* per_sample,
                             cudaStream_t st);
 
 // out[f] = (mean phi_S, mean phi_T, SE_S, SE_T, mean survival) over

@@ -176,6 +176,7 @@ rp_status run_static(const rp::HostSystem& hs, int n_fields, const double* field
   const size_t vec = (size_t)Z * 8;
   const size_t fixed = up256((size_t)items * 3 * sizeof(double)) + up256((size_t)n_fields * 5 * sizeof(double)) +
                        up256(2 * (size_t)n_fields * sizeof(long long)) +
+                       up256(sizeof(rp::HamDev<T>)) + up256(sizeof(rp::LayoutDev)) + up256(sizeof(double)) +
                        up256((size_t)n_fields * sizeof(rp::FieldDev<T>)) +
                        up256((size_t)n_fields * n_c * 2 * sizeof(T)) +
                        up256((size_t)n_fields * n_c * n_c * 2 * sizeof(double));
@@ -241,6 +242,14 @@ rp_status run_static(const rp::HostSystem& hs, int n_fields, const double* field
 
   const rp::HamDev<T> H = ham_of<T>(hs);
   const rp::LayoutDev L = layout_of(hs);
+  auto* d_ham = b.get<rp::HamDev<T>>(1);
+  auto* d_lay = b.get<rp::LayoutDev>(1);
+  double* d_kS = b.get<double>(1);
+  sck(cudaMemcpyAsync(d_ham, &H, sizeof(H), cudaMemcpyHostToDevice, st), "h2d");
+  sck(cudaMemcpyAsync(d_lay, &L, sizeof(L), cudaMemcpyHostToDevice, st), "h2d");
+  sck(cudaMemcpyAsync(d_kS, &hs.k_S, sizeof(double), cudaMemcpyHostToDevice, st), "h2d");
+  h2d += (long long)(sizeof(H) + sizeof(L) + sizeof(double));
+  const rp::SysTab<T> SYS{d_ham, d_lay, d_kS, nullptr, Z, o.pair_id, nullptr};
   std::vector<int> h_field(R);
   std::vector<int2> h_win(R);
   std::vector<long long> h_sample(R), h_out(R);
@@ -265,9 +274,9 @@ rp_status run_static(const rp::HostSystem& hs, int n_fields, const double* field
     // the array keeps the previous call's contents: integrals restart at zero
     L1(rp::launch_zero(d_int, 2 * R, st), "zero integrals");
     if (!o.deterministic)
-      L1(rp::launch_coherent_amps(L, d_sample, nullptr, rows, seed, o.pair_id, amps, nullptr, st),
+      L1(rp::launch_coherent_amps<T>(SYS, d_sample, nullptr, rows, seed, amps, nullptr, st),
          "amplitudes");
-    L1(rp::launch_init_state<T>(L, amps, d_sample, nullptr, d_win, rows, o.deterministic, S0, S1,
+    L1(rp::launch_init_state<T>(SYS, amps, d_sample, nullptr, d_win, rows, o.deterministic, S0, S1,
                                 nullptr, nullptr, st),
        "initial states");
     T* Sb[2] = {S0, S1};
@@ -279,7 +288,7 @@ rp_status run_static(const rp::HostSystem& hs, int n_fields, const double* field
       for (int r = 0; r < rows; ++r) act += (k < h_win[r].y) ? 1 : 0;
       for (int n = 1; n < n_c; ++n) {
         const int mode = (n == 1) ? rp::MODE_FIRST : (n == n_c - 1 ? rp::MODE_LAST : rp::MODE_MID);
-        L1(rp::launch_step<T>(H, d_fdev, d_field, d_win, (int)k, rows, phi[(n - 1) % 3],
+        L1(rp::launch_step<T>(SYS, &H, H.aniso, d_fdev, d_field, d_win, (int)k, rows, phi[(n - 1) % 3],
                               n >= 2 ? phi[(n - 2) % 3] : nullptr,
                               mode == rp::MODE_LAST ? nullptr : phi[n % 3], Q, X, d_coef, n_c, n,
                               mode, st),
@@ -287,12 +296,12 @@ rp_status run_static(const rp::HostSystem& hs, int n_fields, const double* field
         steps++;
       }
       row_terms += act * n_c;
-      L1(rp::launch_gram_integrate<T>(X, d_W, d_field, d_win, (int)k, rows, Z, n_c, d_int, st),
+      L1(rp::launch_gram_integrate<T>(SYS, X, d_W, d_field, d_win, (int)k, rows, n_c, d_int, st),
          "gram-integral kernel");
     }
-    L1(rp::launch_norm<T>(S0, S1, d_win, nullptr, rows, Z, d_surv, st), "norm kernel");
+    L1(rp::launch_norm<T>(SYS, S0, S1, d_win, nullptr, rows, d_surv, st), "norm kernel");
     rp::RowsDev RD{d_field, d_win, d_sample, d_out, nullptr, d_int, d_surv};
-    L1(rp::launch_finalize(RD, rows, hs.k_S, d_ps, st), "finalize kernel");
+    L1(rp::launch_finalize<T>(SYS, RD, rows, d_ps, st), "finalize kernel");
   }
   {
     std::vector<long long> offcnt(2 * (size_t)n_fields);

@@ -66,6 +66,11 @@ class rp_cv_options(C.Structure):
                 ("init_seed", C.c_uint64), ("stream", C.c_void_p)]
 
 
+class rp_cv_plan(C.Structure):
+    _fields_ = [("M_train", C.c_int), ("cv_threshold", C.c_int), ("n_mc", C.c_longlong),
+                ("net", rp_cv_options)]
+
+
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
 FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
 
@@ -112,6 +117,15 @@ SIGNATURES = [
                                  C.POINTER(C.c_longlong), C.POINTER(C.c_double),
                                  C.POINTER(C.c_double), C.POINTER(C.c_double),
                                  C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    ("rp_cv_default_plan", None, [C.POINTER(rp_cv_plan)]),
+    ("rp_yields_cv", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_double, C.c_int,
+                               C.c_int, C.c_uint64, C.c_double, C.POINTER(rp_options),
+                               C.POINTER(rp_cv_plan), C.POINTER(C.c_double), C.POINTER(C.c_int),
+                               C.POINTER(C.c_int), C.POINTER(rp_stats)]),
+    ("rp_yields_batch", C.c_int, [C.c_int, C.POINTER(C.c_void_p), C.POINTER(C.c_int),
+                                  C.POINTER(C.POINTER(C.c_double)), C.POINTER(C.c_int),
+                                  C.POINTER(C.c_double), C.c_uint64, C.POINTER(rp_options),
+                                  C.POINTER(C.POINTER(C.c_double)), C.POINTER(rp_stats)]),
     ("rp_yields_static", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_double), C.c_int,
                                    C.c_uint64, C.c_double, C.POINTER(rp_options),
                                    C.POINTER(C.c_double), C.POINTER(C.c_double),
@@ -436,3 +450,51 @@ class ControlVariate:
         _check(LIB.rp_cv_estimate(self.handle, nf, _lptr(offsets), _lptr(counts), _dptr(per_sample),
                                   _dptr(g), _dptr(mu), _dptr(var_mu), _dptr(out)))
         return out[: nf * 5].reshape(nf, 5)
+
+
+def rp_cv_default_plan(**kw) -> rp_cv_plan:
+    p = rp_cv_plan()
+    LIB.rp_cv_default_plan(C.byref(p))
+    for k, v in kw.items():
+        if k == "net":
+            for kk, vv in v.items():
+                setattr(p.net, kk, vv)
+        else:
+            setattr(p, k, v)
+    return p
+
+
+def rp_yields_cv(h, fields, se_target, M_min, M_max, seed, t_max, opt=None, plan=None):
+    fields = np.ascontiguousarray(fields, dtype=np.float64).reshape(-1)
+    nf = fields.size
+    o = opt if opt is not None else rp_default_options()
+    p = plan if plan is not None else rp_cv_default_plan()
+    out = np.zeros(max(nf * 8, 1))
+    mp = np.zeros(max(nf, 1), dtype=np.int32)
+    mc = np.zeros(max(nf, 1), dtype=np.int32)
+    stats = rp_stats()
+    _check(LIB.rp_yields_cv(h, nf, _dptr(fields), float(se_target), int(M_min), int(M_max),
+                            C.c_uint64(int(seed)), float(t_max), C.byref(o), C.byref(p), _dptr(out),
+                            mp.ctypes.data_as(C.POINTER(C.c_int)),
+                            mc.ctypes.data_as(C.POINTER(C.c_int)), C.byref(stats)))
+    return {"out": out[: nf * 8].reshape(nf, 8), "M_plain": mp[:nf].copy(), "M_cv": mc[:nf].copy(),
+            "stats": stats.as_dict()}
+
+
+def rp_yields_batch(systems, fields, M, t_max, seed, opt=None):
+    """systems: list of System; fields: list of arrays; M, t_max: per system."""
+    n = len(systems)
+    o = opt if opt is not None else rp_default_options()
+    hs = (C.c_void_p * n)(*[s.handle for s in systems])
+    f_arrs = [np.ascontiguousarray(f, dtype=np.float64).reshape(-1) for f in fields]
+    nf = (C.c_int * n)(*[a.size for a in f_arrs])
+    fp = (C.POINTER(C.c_double) * n)(*[_dptr(a) for a in f_arrs])
+    Ms = (C.c_int * n)(*[int(m) for m in M])
+    ts = (C.c_double * n)(*[float(t) for t in t_max])
+    outs = [np.zeros(max(a.size * 5, 1)) for a in f_arrs]
+    op = (C.POINTER(C.c_double) * n)(*[_dptr(a) for a in outs])
+    stats = rp_stats()
+    _check(LIB.rp_yields_batch(n, hs, nf, fp, Ms, ts, C.c_uint64(int(seed)), C.byref(o), op,
+                               C.byref(stats)))
+    return {"out": [o_[: a.size * 5].reshape(a.size, 5) for o_, a in zip(outs, f_arrs)],
+            "stats": stats.as_dict()}

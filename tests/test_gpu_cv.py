@@ -126,3 +126,30 @@ def test_trained_control_variate_gains_and_stays_unbiased():
         exact = dense.trace_yields(s, B, T)[0]
         assert abs(out[i, 0] - exact) < 4 * out[i, 1] + 1e-5
     print("variance reduction per field:", gain)
+
+
+def test_converged_curve_with_control_variate():
+    """rp_yields_cv: every field reaches the combined SE target, control-variate
+    fields need fewer samples than their plain spread asks for, and every
+    estimate agrees with the exact trace (Eq. 14) within 4 SE."""
+    from paper_1612_09517_gb300 import rp
+    w = wl.config1()
+    s = w.system
+    sy = rp.System(s)
+    fields = np.array([0.0, 1.0, 2.0, 5.0])
+    T, se = 3.0, 2e-3
+    plan = rp.rp_cv_default_plan(M_train=128, cv_threshold=64,
+                                 net=dict(hidden=64, layers=3, epochs=60, lr=2e-3))
+    r = rp.rp_yields_cv(sy.handle, fields, se, 8, 20000, 7, T,
+                        rp.rp_default_options(precision="fp32"), plan)
+    out = r["out"]
+    assert np.all(out[:, 1] <= se * 1.0001)
+    used_cv = out[:, 7] > 0
+    assert used_cv.any()
+    for i, B in enumerate(fields):
+        exact = dense.trace_yields(s, B, T)[0]
+        assert abs(out[i, 0] - exact) < 4 * out[i, 1] + 1e-5
+        if used_cv[i]:
+            plain_need = (out[i, 3] ** 2 * r["M_plain"][i]) / se ** 2
+            assert r["M_plain"][i] + r["M_cv"][i] < plain_need
+    print("M_plain", r["M_plain"], "M_cv", r["M_cv"], "beta", out[:, 6])

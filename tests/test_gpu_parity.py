@@ -257,3 +257,30 @@ def test_converged_curve_meets_target_and_matches_plain_runs():
     psi0 = coherent.sample_states(s, 5, range(int(used[0])))
     phS, _, _ = dense.sample_yields(s, fields[0], 3.0, psi0)
     assert abs(r["out"][0, 0] - phS.mean()) < 1e-10
+
+
+# ------------------------------------------- several systems of uneven size
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_batch_of_uneven_systems_matches_single_runs(prec):
+    """rp_yields_batch over systems of different Z, spins, tensors, rates and
+    horizons equals rp_yields of each system with pair word pair_id + s."""
+    rp = _rp()
+    systems = [wl.config1().system,
+               wl.random_anisotropic(2, 1, two_I=[1, 2, 1], k_S=2.0, k_T=0.5, J=0.3, seed=40),
+               wl.random_isotropic(1, 2, two_I=[3, 1, 2], k_S=0.2, k_T=5.0, J=-0.5, seed=41),
+               wl.random_isotropic(5, 4, seed=43, k_S=1.0, k_T=0.3)]
+    sys_h = [rp.System(s) for s in systems]
+    fields = [np.array([0.0, 2.0]), np.array([1.0]), np.array([0.5, 3.0, 7.0]), np.array([0.0, 4.0])]
+    M = [5, 3, 4, 2]
+    T = [2.0, 1.5, 1.0, 0.8]
+    o = rp.rp_default_options(precision=prec, pair_id=10)
+    r = rp.rp_yields_batch(sys_h, fields, M, T, 77, o)
+    tol = TOL[prec]
+    for s in range(len(systems)):
+        single = sys_h[s].yields(fields[s], M[s], 77, T[s], precision=prec, pair_id=10 + s)
+        assert np.allclose(r["out"][s], single["out"], rtol=tol, atol=tol * 1e-2), s
+    # and the oracle agrees for the smallest system
+    psi0 = coherent.sample_states(systems[1], 77, range(3), pair=11)
+    phS, _, _ = dense.sample_yields(systems[1], 1.0, 1.5, psi0)
+    assert abs(r["out"][1][0, 0] - phS.mean()) < tol
