@@ -80,6 +80,10 @@ typedef struct rp_options {
   uint32_t pair_id;       /* Philox counter word 3 (radical-pair id) */
   int profile;            /* 1: time the H.psi step kernels with CUDA events */
   void* stream;           /* cudaStream_t, NULL: per-thread default stream */
+  int kernel;             /* 0: choose; 1: one launch per Chebyshev term (any Z);
+                             2: a whole macro-step per launch with each row's
+                             vectors in shared memory (Z <= 2048 FP32, 1024 FP64;
+                             larger Z falls back to 1) */
 } rp_options;
 
 /* Per-call statistics (optional output of rp_yields). */
@@ -125,7 +129,8 @@ const char* rp_status_str(rp_status s);
 const char* rp_last_error(void);
 
 /* Fill *opt with defaults: RP_FP32, n_cheb 0, tol 0, max_rows 0,
- * deterministic 0, sample_offset 0, pair_id 0, profile 0, stream NULL. */
+ * deterministic 0, sample_offset 0, pair_id 0, profile 0, stream NULL,
+ * kernel 0. */
 void rp_default_options(rp_options* opt);
 
 /* Route the library's device allocations through the caller's allocator

@@ -155,6 +155,8 @@ rp::LayoutDev make_layout(const rp::HostSystem& s) {
 }
 
 int default_ncheb(int precision) { return precision == RP_FP64 ? 64 : 88; }
+
+bool bad_kernel_choice(const rp_options& o) { return o.kernel < 0 || o.kernel > 2; }
 double default_tol(int precision) { return precision == RP_FP64 ? 1e-15 : 1e-9; }
 
 // One work item: a (field, sample) propagation over the whole horizon.
@@ -259,6 +261,8 @@ class YieldEngine {
     X_ = ar_.get<T>((size_t)R * n_c_ * Zslot_ * 2);
     amps_ = ar_.get<double>((size_t)R * rp::kMaxNucDev * 10 * 2);
     row_sys_ = ar_.get<int>(R);
+    small_ = (o_.kernel == 2 || (o_.kernel == 0 && Zslot_ <= rp::small_max_configs<T>())) &&
+             Zslot_ <= rp::small_max_configs<T>();
     S_ = rp::SysTab<T>{d_ham_, d_lay_, d_kS_, row_sys_, Zslot_, o_.pair_id, d_pair_};
     rows_.field = ar_.get<int>(R);
     rows_.win = ar_.get<int2>(R);
@@ -331,7 +335,16 @@ class YieldEngine {
         ck(cudaEventRecord(a, st_), "cudaEventRecord");
       }
       double bytes = 0.0;
-      for (int n = 1; n < n_c_; ++n) {
+      if (small_) {
+        // the whole macro-step on chip: HBM traffic is psi in, psi out and the singlet slices
+        launched(rp::launch_macro_small<T>(S_, sys_.size() == 1 ? &ham1_ : nullptr, aniso_,
+                                           d_fdev_, rows_.field, rows_.win, k, R, P, Q, X_,
+                                           d_coef_, n_c_, st_),
+                 "macro-step kernel");
+        step_launches++;
+        bytes = (2.0 + 0.25 * n_c_) * vbytes;
+      }
+      for (int n = 1; n < n_c_ && !small_; ++n) {
         const int mode = (n == 1) ? rp::MODE_FIRST : (n == n_c_ - 1 ? rp::MODE_LAST : rp::MODE_MID);
         launched(rp::launch_step<T>(S_, sys_.size() == 1 ? &ham1_ : nullptr, aniso_, d_fdev_,
                                     rows_.field, rows_.win, k, R,
@@ -345,7 +358,7 @@ class YieldEngine {
       if (o_.profile) {
         ck(cudaEventRecord(pev.back(), st_), "cudaEventRecord");
         pev_bytes.push_back(bytes);
-        pev_launches.push_back(n_c_ - 1);
+        pev_launches.push_back(small_ ? 1 : n_c_ - 1);
       }
       step_bytes_all += bytes;
       row_terms += act * (long long)n_c_;
@@ -401,6 +414,7 @@ class YieldEngine {
   int* row_sys_ = nullptr;
   uint32_t* d_pair_ = nullptr;
   rp::HamDev<T> ham1_{};
+  bool small_ = false;
   rp::SysTab<T> S_{};
   uint64_t seed_ = 0;
   int R_ = 0;
@@ -1214,6 +1228,7 @@ rp_status rp_yields(rp_system* s, int n_fields, const double* fields, int M, uin
   if (!s) return fail(RP_EINVAL, "system is NULL");
   if (n_fields < 0) return fail(RP_EINVAL, "n_fields must be >= 0");
   if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
+  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0, 1 or 2");
   if (!o.deterministic && M < 2) return fail(RP_EINVAL, "M must be >= 2 (the standard error needs it)");
   if (!(t_max > 0.0) || !std::isfinite(t_max)) return fail(RP_EINVAL, "t_max must be positive and finite");
   if (o.sample_offset < 0) return fail(RP_EINVAL, "sample_offset must be >= 0");
@@ -1245,6 +1260,7 @@ rp_status rp_yields_converged(rp_system* s, int n_fields, const double* fields, 
   if (!s) return fail(RP_EINVAL, "system is NULL");
   if (n_fields < 0) return fail(RP_EINVAL, "n_fields must be >= 0");
   if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
+  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0, 1 or 2");
   if (o.deterministic) return fail(RP_EINVAL, "rp_yields_converged samples coherent states only");
   if (!(se_target > 0.0) || !std::isfinite(se_target)) return fail(RP_EINVAL, "se_target must be positive");
   if (M_min < 2 || M_max < M_min) return fail(RP_EINVAL, "need 2 <= M_min <= M_max");
@@ -1293,6 +1309,7 @@ rp_status rp_yields_cv(rp_system* s, int n_fields, const double* fields, double 
   if (!s) return fail(RP_EINVAL, "system is NULL");
   if (n_fields < 0) return fail(RP_EINVAL, "n_fields must be >= 0");
   if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
+  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0, 1 or 2");
   if (o.deterministic) return fail(RP_EINVAL, "rp_yields_cv samples coherent states only");
   if (!(se_target > 0.0) || !std::isfinite(se_target)) return fail(RP_EINVAL, "se_target must be positive");
   if (M_min < 2 || M_max < M_min) return fail(RP_EINVAL, "need 2 <= M_min <= M_max");
@@ -1332,6 +1349,7 @@ rp_status rp_yields_batch(int n_sys, rp_system* const* systems, const int* n_fie
   if (n_sys == 0) return RP_OK;
   if (!systems || !n_fields || !fields || !M || !t_max || !out) return fail(RP_EINVAL, "NULL argument");
   if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
+  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0, 1 or 2");
   if (o.deterministic) return fail(RP_EINVAL, "rp_yields_batch samples coherent states only");
   if (o.sample_offset < 0) return fail(RP_EINVAL, "sample_offset must be >= 0");
   long long total = 0;

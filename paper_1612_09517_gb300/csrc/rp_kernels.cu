@@ -254,6 +254,58 @@ __device__ __forceinline__ void half_nucleus(Cx<T> (&y)[4], T (&b1)[3], T (&b2)[
   }
 }
 
+// z = (H' a - E_c a) / dE from the partner sum y and the local fields b1, b2:
+// adds the electron block omega (S1z + S2z) + 2J S1.S2 - i kappa (2 P_S - 1) and
+// the diagonal-in-m hyperfine part (S1 . b1) x 1 + 1 x (S2 . b2),
+// b_i = sum_k M_k A_k e_z, then applies the Chebyshev scaling of field F.
+template <typename T, bool ANISO>
+__device__ __forceinline__ void finish_z(const HamDev<T>& H, const FieldDev<T>& F,
+                                         const Cx<T> (&a)[4], Cx<T> (&y)[4], const T (&b1)[3],
+                                         const T (&b2)[3], Cx<T> (&z)[4]) {
+  // electron block: omega (S1z + S2z) + 2J S1.S2 - i kappa (2 P_S - 1), plus the
+  // diagonal-in-m hyperfine part (S1 . b1) x 1 + 1 x (S2 . b2), b_i = sum_k M_k A_k e_z
+  const T w = F.omega, Je = H.Je, kp = H.kappa, hJ = T(0.5) * Je;
+  if (ANISO) {
+    cmac(y[0], w + hJ, kp, a[0]);
+    cmac(y[1], -hJ, T(0), a[1]);
+    cmac(y[1], Je, kp, a[2]);
+    cmac(y[2], Je, kp, a[1]);
+    cmac(y[2], -hJ, T(0), a[2]);
+    cmac(y[3], -w + hJ, kp, a[3]);
+    const T h = T(0.5);
+#pragma unroll
+    for (int e2 = 0; e2 < 2; ++e2) {
+      const Cx<T> lo = a[e2], hi = a[2 + e2];
+      cmac(y[e2], h * b1[2], T(0), lo);
+      cmac(y[e2], h * b1[0], -h * b1[1], hi);
+      cmac(y[2 + e2], h * b1[0], h * b1[1], lo);
+      cmac(y[2 + e2], -h * b1[2], T(0), hi);
+    }
+#pragma unroll
+    for (int e1 = 0; e1 < 2; ++e1) {
+      const Cx<T> lo = a[2 * e1], hi = a[2 * e1 + 1];
+      cmac(y[2 * e1], h * b2[2], T(0), lo);
+      cmac(y[2 * e1], h * b2[0], -h * b2[1], hi);
+      cmac(y[2 * e1 + 1], h * b2[0], h * b2[1], lo);
+      cmac(y[2 * e1 + 1], -h * b2[2], T(0), hi);
+    }
+  } else {
+    const T sp = T(0.5) * (b1[2] + b2[2]), sm = T(0.5) * (b1[2] - b2[2]);
+    cmac(y[0], w + hJ + sp, kp, a[0]);
+    cmac(y[1], -hJ + sm, T(0), a[1]);
+    cmac(y[1], Je, kp, a[2]);
+    cmac(y[2], Je, kp, a[1]);
+    cmac(y[2], -hJ - sm, T(0), a[2]);
+    cmac(y[3], -w + hJ - sp, kp, a[3]);
+  }
+  // z = s y - sh a
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    z[e].re = F.s * y[e].re - (F.sh_re * a[e].re - F.sh_im * a[e].im);
+    z[e].im = F.s * y[e].im - (F.sh_re * a[e].im + F.sh_im * a[e].re);
+  }
+}
+
 // Body of one Chebyshev term; H is either the kernel-parameter copy (one
 // system per launch) or a shared-memory copy of the row's system.
 template <typename T, bool ANISO>
@@ -379,50 +431,9 @@ __device__ __forceinline__ void step_body(const HamDev<T>& H, const SysTab<T>& S
       add_partner<T, ANISO>(y, c, m - st, rr, H.U[p], sqrt(I * (I + 1) - M * (M + 1)), false);
   }
 
-  // electron block: omega (S1z + S2z) + 2J S1.S2 - i kappa (2 P_S - 1), plus the
-  // diagonal-in-m hyperfine part (S1 . b1) x 1 + 1 x (S2 . b2), b_i = sum_k M_k A_k e_z
   const FieldDev<T> F = fields[f];
-  const T w = F.omega, Je = H.Je, kp = H.kappa, hJ = T(0.5) * Je;
-  if (ANISO) {
-    cmac(y[0], w + hJ, kp, a[0]);
-    cmac(y[1], -hJ, T(0), a[1]);
-    cmac(y[1], Je, kp, a[2]);
-    cmac(y[2], Je, kp, a[1]);
-    cmac(y[2], -hJ, T(0), a[2]);
-    cmac(y[3], -w + hJ, kp, a[3]);
-    const T h = T(0.5);
-#pragma unroll
-    for (int e2 = 0; e2 < 2; ++e2) {
-      const Cx<T> lo = a[e2], hi = a[2 + e2];
-      cmac(y[e2], h * b1[2], T(0), lo);
-      cmac(y[e2], h * b1[0], -h * b1[1], hi);
-      cmac(y[2 + e2], h * b1[0], h * b1[1], lo);
-      cmac(y[2 + e2], -h * b1[2], T(0), hi);
-    }
-#pragma unroll
-    for (int e1 = 0; e1 < 2; ++e1) {
-      const Cx<T> lo = a[2 * e1], hi = a[2 * e1 + 1];
-      cmac(y[2 * e1], h * b2[2], T(0), lo);
-      cmac(y[2 * e1], h * b2[0], -h * b2[1], hi);
-      cmac(y[2 * e1 + 1], h * b2[0], h * b2[1], lo);
-      cmac(y[2 * e1 + 1], -h * b2[2], T(0), hi);
-    }
-  } else {
-    const T sp = T(0.5) * (b1[2] + b2[2]), sm = T(0.5) * (b1[2] - b2[2]);
-    cmac(y[0], w + hJ + sp, kp, a[0]);
-    cmac(y[1], -hJ + sm, T(0), a[1]);
-    cmac(y[1], Je, kp, a[2]);
-    cmac(y[2], Je, kp, a[1]);
-    cmac(y[2], -hJ - sm, T(0), a[2]);
-    cmac(y[3], -w + hJ - sp, kp, a[3]);
-  }
-  // z = s y - sh a
   Cx<T> z[4];
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    z[e].re = F.s * y[e].re - (F.sh_re * a[e].re - F.sh_im * a[e].im);
-    z[e].im = F.s * y[e].im - (F.sh_re * a[e].im + F.sh_im * a[e].re);
-  }
+  finish_z<T, ANISO>(H, F, a, y, b1, b2, z);
   const size_t off = row0 + (size_t)m * 8;
   if (mode == MODE_APPLY) {
     store4(next + off, z);
@@ -462,6 +473,169 @@ __device__ __forceinline__ void step_body(const HamDev<T>& H, const SysTab<T>& S
   for (int e = 0; e < 4; ++e) cmac(s[e], cr, ci, ph[e]);
   store4(acc + off, s);
   store_singlet(xr + ((size_t)n * Zs + m) * 2, ph);
+}
+
+// ---- whole macro-steps of small systems in one CTA per row ----
+// For Z <= kSmallMax (FP32 2048, FP64 1024 configurations) one CTA holds a
+// row's phi_{n-1}, phi_{n-2} / phi_n and the accumulator in shared memory
+// (16-byte planes) and runs every term of a macro-step between block
+// barriers: each term reads the partners of every nucleus from shared memory,
+// phi_{n-2} is read from the buffer that receives phi_n (same thread, same
+// entry), and the singlet slices go to X for the Gram kernel as in k_cheb_step.
+template <typename T>
+struct SmallCfg {
+  static constexpr int kMax = sizeof(T) == 4 ? 2048 : 1024;
+  static constexpr int kThreads = 256;
+};
+
+template <typename T, bool ANISO>
+__device__ __forceinline__ void apply_local(const HamDev<T>& H, const FieldDev<T>& F, unsigned m,
+                                            const Cx<T> (&a)[4], const Cx<T>* buf, int nbuf,
+                                            Cx<T> (&z)[4]) {
+  Cx<T> y[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) y[e] = {T(0), T(0)};
+  T b1[3] = {T(0), T(0), T(0)}, b2[3] = {T(0), T(0), T(0)};
+  for (int p = 0; p < H.n_half; ++p) {
+    const unsigned j = (m >> p) & 1u;
+    Cx<T> q[4];
+    tile_get(buf, nbuf, (int)(m ^ (1u << p)), q);
+    half_nucleus<T, ANISO>(y, b1, b2, H, p, j, q);
+  }
+  unsigned qd = m >> H.n_half;
+  const T s2 = T(1.41421356237309504880);
+  for (int p = H.n_half; p < H.n_half + H.n_one; ++p) {
+    const unsigned j = qd % 3u;
+    qd /= 3u;
+    const int rr = H.rad[p];
+    const unsigned st = (unsigned)H.stride[p];
+    if (ANISO) {
+      add_field(b1, b2, rr, T(1) - T(j), H.v[p]);
+    } else {
+      const T dz = (T(1) - T(j)) * H.v[p][2];
+      if (rr == 0) b1[2] += dz;
+      else b2[2] += dz;
+    }
+    Cx<T> q[4];
+    if (j < 2u) {
+      tile_get(buf, nbuf, (int)(m + st), q);
+      add_partner_q<T, ANISO>(y, q, rr, H.U[p], s2, true);
+    }
+    if (j > 0u) {
+      tile_get(buf, nbuf, (int)(m - st), q);
+      add_partner_q<T, ANISO>(y, q, rr, H.U[p], s2, false);
+    }
+  }
+  for (int p = H.n_half + H.n_one; p < H.n_nuc; ++p) {
+    const unsigned d = (unsigned)H.d[p];
+    const unsigned j = qd % d;
+    qd /= d;
+    const int rr = H.rad[p];
+    const unsigned st = (unsigned)H.stride[p];
+    const T I = T(0.5) * T(d - 1), M = I - T(j);
+    add_field(b1, b2, rr, M, H.v[p]);
+    Cx<T> q[4];
+    if (j + 1u < d) {
+      tile_get(buf, nbuf, (int)(m + st), q);
+      add_partner_q<T, ANISO>(y, q, rr, H.U[p], sqrt(I * (I + 1) - M * (M - 1)), true);
+    }
+    if (j > 0u) {
+      tile_get(buf, nbuf, (int)(m - st), q);
+      add_partner_q<T, ANISO>(y, q, rr, H.U[p], sqrt(I * (I + 1) - M * (M + 1)), false);
+    }
+  }
+  finish_z<T, ANISO>(H, F, a, y, b1, b2, z);
+}
+
+template <typename T, bool ANISO>
+__device__ __forceinline__ void macro_small_body(const HamDev<T>& H, const SysTab<T>& S,
+                                                 const FieldDev<T>& F, int r,
+                                                 const T* __restrict__ P, T* __restrict__ Q,
+                                                 T* __restrict__ X, const T* __restrict__ cf,
+                                                 int n_c) {
+  extern __shared__ __align__(16) unsigned char small_smem[];
+  const int Z = (int)H.Z;
+  Cx<T>* bufA = reinterpret_cast<Cx<T>*>(small_smem);  // 4 complex per configuration
+  Cx<T>* bufB = bufA + (size_t)4 * Z;
+  Cx<T>* accb = bufB + (size_t)4 * Z;
+  const size_t row0 = (size_t)r * S.Zslot * 8;
+  const size_t Zs = (size_t)S.Zslot;
+  T* xr = X + (size_t)r * n_c * Zs * 2;
+  const T c0r = cf[0], c0i = cf[1];
+  for (int m = threadIdx.x; m < Z; m += blockDim.x) {
+    Cx<T> a[4];
+    load4(P + row0 + (size_t)m * 8, a);
+    tile_put(bufA, Z, m, a);
+    Cx<T> s[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      s[e] = {T(0), T(0)};
+      cmac(s[e], c0r, c0i, a[e]);
+    }
+    tile_put(accb, Z, m, s);
+    store_singlet(xr + (size_t)m * 2, a);
+  }
+  __syncthreads();
+  for (int n = 1; n < n_c; ++n) {
+    const Cx<T>* cur = (n & 1) ? bufA : bufB;  // phi_{n-1}
+    Cx<T>* nxt = (n & 1) ? bufB : bufA;        // phi_{n-2}, then phi_n
+    const T cr = cf[2 * n], ci = cf[2 * n + 1];
+    for (int m = threadIdx.x; m < Z; m += blockDim.x) {
+      Cx<T> a[4], z[4], ph[4];
+      tile_get(cur, Z, m, a);
+      apply_local<T, ANISO>(H, F, (unsigned)m, a, cur, Z, z);
+      if (n == 1) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) ph[e] = z[e];
+      } else {
+        Cx<T> pv[4];
+        tile_get(nxt, Z, m, pv);
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          ph[e].re = T(2) * z[e].re - pv[e].re;
+          ph[e].im = T(2) * z[e].im - pv[e].im;
+        }
+      }
+      Cx<T> s[4];
+      tile_get(accb, Z, m, s);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) cmac(s[e], cr, ci, ph[e]);
+      tile_put(accb, Z, m, s);
+      store_singlet(xr + ((size_t)n * Zs + m) * 2, ph);
+      if (n < n_c - 1) tile_put(nxt, Z, m, ph);
+    }
+    __syncthreads();
+  }
+  for (int m = threadIdx.x; m < Z; m += blockDim.x) {
+    Cx<T> s[4];
+    tile_get(accb, Z, m, s);
+    store4(Q + row0 + (size_t)m * 8, s);
+  }
+}
+
+template <typename T, bool ANISO, bool MULTI>
+__global__ void __launch_bounds__(256) k_macro_small(
+    const SysTab<T> S, const HamDev<T> H1, const FieldDev<T>* __restrict__ fields,
+    const int* __restrict__ row_field, const int2* __restrict__ row_win, int macro,
+    const T* __restrict__ P, T* __restrict__ Q, T* __restrict__ X, const T* __restrict__ coef,
+    int n_c) {
+  const int r = blockIdx.x;
+  const int2 w = row_win[r];
+  if (macro < w.x || macro >= w.y) return;
+  const int f = row_field[r];
+  const FieldDev<T> F = fields[f];
+  const T* cf = coef + (size_t)f * n_c * 2;
+  if (MULTI) {
+    __shared__ HamDev<T> Hs;
+    const int sidx = S.row_sys ? S.row_sys[r] : 0;
+    const int4* src = reinterpret_cast<const int4*>(S.ham + sidx);
+    int4* dst = reinterpret_cast<int4*>(&Hs);
+    for (int i = threadIdx.x; i < (int)(sizeof(HamDev<T>) / 16); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    macro_small_body<T, ANISO>(Hs, S, F, r, P, Q, X, cf, n_c);
+  } else {
+    macro_small_body<T, ANISO>(H1, S, F, r, P, Q, X, cf, n_c);
+  }
 }
 
 template <int NT>
@@ -869,6 +1043,43 @@ cudaError_t launch_step(const SysTab<T>& S, const HamDev<T>* one, int aniso,
 }
 
 template <typename T>
+int small_max_configs() {
+  return SmallCfg<T>::kMax;
+}
+
+template <typename T>
+cudaError_t launch_macro_small(const SysTab<T>& S, const HamDev<T>* one, int aniso,
+                               const FieldDev<T>* fields, const int* row_field,
+                               const int2* row_win, int macro, int rows, const T* P, T* Q, T* X,
+                               const T* coef, int n_c, cudaStream_t st) {
+  if (rows == 0) return cudaSuccess;
+  if (S.Zslot > SmallCfg<T>::kMax) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)3 * 4 * S.Zslot * sizeof(Cx<T>);
+  int b = 32;
+  while (b < SmallCfg<T>::kThreads && b < S.Zslot) b *= 2;
+  HamDev<T> h1;
+  if (one) h1 = *one;
+  else std::memset(&h1, 0, sizeof(h1));
+#define RP_LAUNCH_SMALL(AN, MU)                                                                   \
+  {                                                                                                \
+    if (smem > 48 * 1024) {                                                                       \
+      cudaError_t e = cudaFuncSetAttribute(k_macro_small<T, AN, MU>,                              \
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+      if (e != cudaSuccess) return e;                                                            \
+    }                                                                                              \
+    k_macro_small<T, AN, MU><<<rows, b, smem, st>>>(S, h1, fields, row_field, row_win, macro, P,  \
+                                                    Q, X, coef, n_c);                              \
+  }
+  if (one) {
+    if (aniso) RP_LAUNCH_SMALL(true, false) else RP_LAUNCH_SMALL(false, false)
+  } else {
+    if (aniso) RP_LAUNCH_SMALL(true, true) else RP_LAUNCH_SMALL(false, true)
+  }
+#undef RP_LAUNCH_SMALL
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_gram_integrate(const SysTab<T>& S, const T* X, const double* W,
                                   const int* row_field, const int2* row_win, int macro, int rows,
                                   int n_c, double* integral, cudaStream_t st) {
@@ -936,6 +1147,11 @@ template cudaError_t launch_step<float>(const SysTab<float>&, const HamDev<float
 template cudaError_t launch_gram_integrate<float>(const SysTab<float>&, const float*, const double*,
                                                   const int*, const int2*, int, int, int, double*,
                                                   cudaStream_t);
+template int small_max_configs<float>();
+template cudaError_t launch_macro_small<float>(const SysTab<float>&, const HamDev<float>*, int,
+                                               const FieldDev<float>*, const int*, const int2*, int,
+                                               int, const float*, float*, float*, const float*, int,
+                                               cudaStream_t);
 template cudaError_t launch_norm<float>(const SysTab<float>&, const float*, const float*, const int2*,
                                         const int*, int, double*, cudaStream_t);
 template cudaError_t launch_finalize<float>(const SysTab<float>&, const RowsDev&, int, double*,
@@ -952,6 +1168,11 @@ template cudaError_t launch_step<double>(const SysTab<double>&, const HamDev<dou
 template cudaError_t launch_gram_integrate<double>(const SysTab<double>&, const double*, const double*,
                                                   const int*, const int2*, int, int, int, double*,
                                                   cudaStream_t);
+template int small_max_configs<double>();
+template cudaError_t launch_macro_small<double>(const SysTab<double>&, const HamDev<double>*, int,
+                                               const FieldDev<double>*, const int*, const int2*, int,
+                                               int, const double*, double*, double*, const double*, int,
+                                               cudaStream_t);
 template cudaError_t launch_norm<double>(const SysTab<double>&, const double*, const double*, const int2*,
                                         const int*, int, double*, cudaStream_t);
 template cudaError_t launch_finalize<double>(const SysTab<double>&, const RowsDev&, int, double*,

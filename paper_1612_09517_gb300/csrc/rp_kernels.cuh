@@ -98,6 +98,20 @@ cudaError_t launch_step(const SysTab<T>& S, const HamDev<T>* one, int aniso,
                         int macro, int rows, const T* cur, const T* prev, T* next, T* acc, T* X,
                         const T* coef, int n_c, int n, int mode, cudaStream_t st);
 
+// Largest Z (configurations) that launch_macro_small can hold.
+template <typename T>
+int small_max_configs();
+
+// A whole macro-step (terms 1 .. n_c - 1) of every active row in one launch,
+// one CTA per row with the row's vectors in shared memory (S.Zslot must be
+// <= small_max_configs<T>()): reads psi from P, writes the propagated psi to Q
+// and the singlet slices to X.
+template <typename T>
+cudaError_t launch_macro_small(const SysTab<T>& S, const HamDev<T>* one, int aniso,
+                               const FieldDev<T>* fields, const int* row_field,
+                               const int2* row_win, int macro, int rows, const T* P, T* Q, T* X,
+                               const T* coef, int n_c, cudaStream_t st);
+
 // integral[r] += sum_nm W_nm <x_n|x_m> for the macro-step just finished
 // (x_n = singlet slices X[r][n], W per field); one FP64 atomic per CTA.
 template <typename T>

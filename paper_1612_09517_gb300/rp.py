@@ -35,7 +35,7 @@ class rp_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("n_cheb", C.c_int), ("tol", C.c_double),
                 ("max_rows", C.c_int), ("deterministic", C.c_int),
                 ("sample_offset", C.c_longlong), ("pair_id", C.c_uint32),
-                ("profile", C.c_int), ("stream", C.c_void_p)]
+                ("profile", C.c_int), ("stream", C.c_void_p), ("kernel", C.c_int)]
 
 
 class rp_stats(C.Structure):

@@ -158,16 +158,18 @@ def test_deterministic_trace_matches_oracle():
     assert abs(r["out"][1, 0] - r["out"][2, 0]) < 1e-10
 
 
+@pytest.mark.parametrize("kernel", [1, 2])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("name,mk", MIXED[1:], ids=[m[0] for m in MIXED[1:]])
-def test_mixed_systems_per_sample(name, mk, prec):
-    """Anisotropic tensors, spin 1 and 3/2, J != 0, k_S != k_T, no nuclei, ragged Z."""
+def test_mixed_systems_per_sample(name, mk, prec, kernel):
+    """Anisotropic tensors, spin 1 and 3/2, J != 0, k_S != k_T, no nuclei, ragged Z;
+    per-term launches (kernel 1) and whole macro-steps on chip (kernel 2)."""
     rp = _rp()
     s = mk()
     sy = rp.System(s)
     fields = np.array([0.0, 0.8, 3.0])
     T, M = 2.5, 6
-    r = sy.yields(fields, M, 11, T, per_sample=True, precision=prec)
+    r = sy.yields(fields, M, 11, T, per_sample=True, precision=prec, kernel=kernel)
     psi0 = coherent.sample_states(s, 11, range(M))
     for i, B in enumerate(fields):
         phS, phT, surv = dense.sample_yields(s, B, T, psi0)
@@ -284,3 +286,18 @@ def test_batch_of_uneven_systems_matches_single_runs(prec):
     psi0 = coherent.sample_states(systems[1], 77, range(3), pair=11)
     phS, _, _ = dense.sample_yields(systems[1], 1.0, 1.5, psi0)
     assert abs(r["out"][1][0, 0] - phS.mean()) < tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_kernel_paths_agree(prec):
+    """The on-chip macro-step kernel and the per-term kernels give the same
+    per-sample yields (largest Z that fits on chip included)."""
+    rp = _rp()
+    big = wl.random_isotropic(6, 4, two_I=[1] * 10, seed=44, k_S=1.0, k_T=0.4, J=0.1)  # Z = 1024
+    for s in (wl.config1().system, big):
+        sy = rp.System(s)
+        a = sy.yields([0.0, 2.0], 4, 3, 1.0, per_sample=True, precision=prec, kernel=1)
+        b = sy.yields([0.0, 2.0], 4, 3, 1.0, per_sample=True, precision=prec, kernel=2)
+        tol = 1e-12 if prec == "fp64" else 2e-6
+        assert np.allclose(a["per_sample"], b["per_sample"], rtol=tol, atol=tol * 1e-2)
+        assert b["stats"]["step_launches"] < a["stats"]["step_launches"]
