@@ -82,8 +82,23 @@ typedef struct rp_options {
   void* stream;           /* cudaStream_t, NULL: per-thread default stream */
   int kernel;             /* 0: choose; 1: one launch per Chebyshev term (any Z);
                              2: a whole macro-step per launch with each row's
-                             vectors in shared memory (Z <= 2048 FP32, 1024 FP64;
-                             larger Z falls back to 1) */
+                             vectors in shared memory (Z <= 2048 FP32, 1024
+                             FP64; larger Z falls back to 1); 3: as 1, and FP32
+                             single systems with >= 8 spin-1/2 nuclei stage
+                             each block's partner configurations with bulk
+                             async copies (slower than 1 on the workloads
+                             measured so far; a candidate of rp_tune) */
+  int gram;               /* time integral (Eqs. 20, 22) of each macro-step: 0 choose
+                             (2 where it applies); 1 CUDA cores (any precision);
+                             2 tensor cores (FP32 single systems with the
+                             per-term kernels and n_cheb <= 96: tcgen05.mma
+                             kind::tf32 on hi/lo-split values, FP32 partial
+                             sums, FP64 contraction; otherwise falls back to 1) */
+  int graph;              /* 1: capture each macro-step's launches (Chebyshev terms
+                             and time integral) in a CUDA graph and replay it; the
+                             kernels then read the macro-step index from a device
+                             counter.  Refill work between macro-steps stays eager.
+                             Results are identical to graph = 0. */
 } rp_options;
 
 /* Per-call statistics (optional output of rp_yields). */
@@ -100,6 +115,8 @@ typedef struct rp_stats {
   int n_cheb;                   /* Chebyshev terms per macro-step used */
   long long h2d_bytes;          /* host-to-device bytes copied by the call */
   long long d2h_bytes;          /* device-to-host bytes copied by the call */
+  long long graph_launches;     /* macro-steps replayed from a CUDA graph (graph = 1);
+                                   their kernels are counted in kernel_launches */
 } rp_stats;
 
 /* Propagation plan of one field (rp_plan_field; host logic, no GPU needed). */
@@ -360,6 +377,41 @@ rp_status rp_yields_cv(rp_system* sys, int n_fields, const double* fields, doubl
 rp_status rp_yields_static(rp_system* sys, int n_fields, const double* fields, int M,
                            uint64_t seed, double t_max, const rp_options* opt, double* out,
                            double* per_sample, rp_stats* stats);
+
+/* Launch-configuration autotuner (the paper has no counterpart: its method
+ * ran serially on CPUs).  For one system, precision and concurrency it times
+ * the candidates
+ *   kernel in {1, 2 (only if Z fits in shared memory), 3 (only FP32 with
+ *   >= 8 spin-1/2 nuclei, where it stages partner tiles)},
+ *   n_cheb in {32, 48, 64, 88},  graph in {0, 1}
+ * on `rows` coherent-state samples at field B (mT) over six macro-steps
+ * through rp_yields (one untimed run, the faster of two timed runs by the
+ * call's CUDA events) and keeps the one with the most propagated
+ * sample-microseconds per second.  Every candidate meets the same truncation
+ * tolerance, so the choice changes speed, not results beyond rounding.
+ *   base   options to start from (NULL: defaults); precision, tol, stream and
+ *          deterministic are kept, kernel/n_cheb/graph are chosen and
+ *          max_rows is set to rows
+ *   tuned  [out] base with the chosen settings
+ *   res    [out, may be NULL] the choice, its rate, the rate of base's own
+ *          settings (-1 if base's settings were not a candidate) and the
+ *          number of candidates timed
+ * If the environment variable RP_TUNE_CACHE names a file, results are looked
+ * up there first (key: device name and SM count, precision, sorted spins,
+ * anisotropy, Z, rows, |B| to 3 digits, deterministic) and new results are
+ * appended; a hit times nothing (res->from_cache = 1).
+ * Errors: RP_EINVAL (rows < 2, bad precision, non-finite B, NULL), plus any
+ * error of rp_plan_field / rp_yields. */
+typedef struct rp_tune_result {
+  int kernel, n_cheb, graph;
+  double rate;       /* propagated sample-us per second of device time */
+  double base_rate;  /* same for base's own settings, -1 if not timed */
+  int candidates;    /* candidates timed (0 on a cache hit) */
+  int from_cache;
+} rp_tune_result;
+
+rp_status rp_tune(rp_system* sys, double B, int rows, const rp_options* base,
+                  rp_options* tuned, rp_tune_result* res);
 
 #ifdef __cplusplus
 }

@@ -59,7 +59,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     for f in cpp:
         o = os.path.join(BUILDDIR, f + ".o")
         objs.append(o)
-        cmd = ["g++", "-O2", "-fPIC", "-std=c++17", *inc, "-c", os.path.join(CSRC, f), "-o", o]
+        cuda_inc = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "include")
+        cmd = ["g++", "-O2", "-fPIC", "-std=c++17", *inc, "-I", cuda_inc, "-c",
+               os.path.join(CSRC, f), "-o", o]
         jobs.append(cmd)
     procs = [subprocess.Popen(c, stdout=subprocess.PIPE, stderr=subprocess.STDOUT) for c in jobs]
     failed = []

@@ -156,7 +156,9 @@ rp::LayoutDev make_layout(const rp::HostSystem& s) {
 
 int default_ncheb(int precision) { return precision == RP_FP64 ? 64 : 88; }
 
-bool bad_kernel_choice(const rp_options& o) { return o.kernel < 0 || o.kernel > 2; }
+bool bad_kernel_choice(const rp_options& o) {
+  return o.kernel < 0 || o.kernel > 3 || o.graph < 0 || o.graph > 1 || o.gram < 0 || o.gram > 2;
+}
 double default_tol(int precision) { return precision == RP_FP64 ? 1e-15 : 1e-9; }
 
 // One work item: a (field, sample) propagation over the whole horizon.
@@ -206,7 +208,7 @@ class YieldEngine {
     }
   }
 
-  long long launches = 0, step_launches = 0, row_terms = 0, h2d = 0;
+  long long launches = 0, step_launches = 0, row_terms = 0, h2d = 0, d2h = 0;
   double step_bytes_all = 0.0;
   std::vector<cudaEvent_t> pev;
   std::vector<double> pev_bytes;
@@ -214,6 +216,8 @@ class YieldEngine {
 
   ~YieldEngine() {
     for (auto e : pev) cudaEventDestroy(e);
+    drop_graphs();
+    if (cap_st_) cudaStreamDestroy(cap_st_);
   }
 
   void set_fields(const std::vector<rp::FieldPlan>& plans) {
@@ -246,7 +250,8 @@ class YieldEngine {
   }
 
   static size_t row_bytes(long long Z, int n_c) {
-    return (4 * (size_t)Z * 8 + (size_t)n_c * Z * 2) * sizeof(T) + 256 + rp::kMaxNucDev * 20 * 8;
+    const size_t x_row = std::max<size_t>((size_t)n_c * Z * 2, rp::xblk_floats_per_row(Z, n_c));
+    return (4 * (size_t)Z * 8 + x_row) * sizeof(T) + 256 + rp::kMaxNucDev * 20 * 8;
   }
 
   long long zslot() const { return Zslot_; }
@@ -258,12 +263,26 @@ class YieldEngine {
     S1_ = ar_.get<T>((size_t)R * vec);
     F1_ = ar_.get<T>((size_t)R * vec);
     F2_ = ar_.get<T>((size_t)R * vec);
-    X_ = ar_.get<T>((size_t)R * n_c_ * Zslot_ * 2);
     amps_ = ar_.get<double>((size_t)R * rp::kMaxNucDev * 10 * 2);
     row_sys_ = ar_.get<int>(R);
     small_ = (o_.kernel == 2 || (o_.kernel == 0 && Zslot_ <= rp::small_max_configs<T>())) &&
              Zslot_ <= rp::small_max_configs<T>();
-    S_ = rp::SysTab<T>{d_ham_, d_lay_, d_kS_, row_sys_, Zslot_, o_.pair_id, d_pair_};
+    // tensor-core time integral: FP32, one system (the slices of every row cover
+    // the same Z, so the zero padding of the last chunk stays zero), per-term kernels
+    tc_gram_ = sizeof(T) == 4 && sys_.size() == 1 && !small_ && o_.gram != 1 &&
+               rp::gram_tc_supported(n_c_);
+    const size_t x_row = std::max<size_t>((size_t)n_c_ * Zslot_ * 2,
+                                          rp::xblk_floats_per_row(Zslot_, n_c_));
+    X_ = ar_.get<T>((size_t)R * x_row);
+    if (tc_gram_) {
+      ck(cudaMemsetAsync(X_, 0, (size_t)R * x_row * sizeof(T), st_), "cudaMemsetAsync");
+      int dev = 0;
+      ck(cudaGetDevice(&dev), "cudaGetDevice");
+      ck(cudaDeviceGetAttribute(&n_sm_, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
+    }
+    d_err_ = ar_.get<int>(1);
+    ck(cudaMemsetAsync(d_err_, 0, sizeof(int), st_), "cudaMemsetAsync");
+    S_ = rp::SysTab<T>{d_ham_, d_lay_, d_kS_, row_sys_, Zslot_, o_.pair_id, d_pair_, d_err_};
     rows_.field = ar_.get<int>(R);
     rows_.win = ar_.get<int2>(R);
     rows_.sample = ar_.get<long long>(R);
@@ -313,6 +332,11 @@ class YieldEngine {
     }
     upload_rows();
     init_flagged();
+    if (o_.graph) {
+      if (!d_macro_) d_macro_ = ar_.get<int>(1);
+      ck(cudaMemsetAsync(d_macro_, 0, sizeof(int), st_), "cudaMemsetAsync");
+      drop_graphs();
+    }
     for (int k = 0; live > 0; ++k) {
       long long act = 0;
       double act_z = 0.0;  // configurations of the active rows
@@ -322,10 +346,6 @@ class YieldEngine {
           act_z += (double)sys_[h_sys[r]]->Z;
         }
       const double vbytes = 8.0 * sizeof(T) * act_z;  // one state vector of every active row
-      T* Sb[2] = {S0_, S1_};
-      T* P = Sb[k & 1];
-      T* Q = Sb[(k + 1) & 1];
-      T* phi[3] = {P, F1_, F2_};
       if (o_.profile) {
         cudaEvent_t a, b;
         ck(cudaEventCreate(&a), "cudaEventCreate");
@@ -337,34 +357,36 @@ class YieldEngine {
       double bytes = 0.0;
       if (small_) {
         // the whole macro-step on chip: HBM traffic is psi in, psi out and the singlet slices
-        launched(rp::launch_macro_small<T>(S_, sys_.size() == 1 ? &ham1_ : nullptr, aniso_,
-                                           d_fdev_, rows_.field, rows_.win, k, R, P, Q, X_,
-                                           d_coef_, n_c_, st_),
-                 "macro-step kernel");
-        step_launches++;
         bytes = (2.0 + 0.25 * n_c_) * vbytes;
+      } else {
+        for (int n = 1; n < n_c_; ++n) bytes += rp::term_vector_passes(n, n_c_) * vbytes;
       }
-      for (int n = 1; n < n_c_ && !small_; ++n) {
-        const int mode = (n == 1) ? rp::MODE_FIRST : (n == n_c_ - 1 ? rp::MODE_LAST : rp::MODE_MID);
-        launched(rp::launch_step<T>(S_, sys_.size() == 1 ? &ham1_ : nullptr, aniso_, d_fdev_,
-                                    rows_.field, rows_.win, k, R,
-                                    phi[(n - 1) % 3], n >= 2 ? phi[(n - 2) % 3] : nullptr,
-                                    mode == rp::MODE_LAST ? nullptr : phi[n % 3], Q, X_, d_coef_,
-                                    n_c_, n, mode, st_),
-                 "step kernel");
-        step_launches++;
-        bytes += (mode == rp::MODE_FIRST ? 3.5 : (mode == rp::MODE_MID ? 5.25 : 4.25)) * vbytes;
+      // profile events bracket the step kernels (eager) or the whole graph replay
+      cudaEvent_t ev_end = o_.profile ? pev.back() : nullptr;
+      int n_step = 0;
+      if (!o_.graph) {
+        n_step = issue(k, st_, nullptr, ev_end);
+        launches += n_step + 1;
+      } else if (k < 2) {
+        // the first macro-step of each parity runs eagerly (kernel attributes get set)
+        n_step = issue(k, st_, d_macro_, ev_end);
+        launches += n_step + 2;
+      } else {
+        const int p = k & 1;
+        if (!gexec_[p]) capture(k, p);
+        ck(cudaGraphLaunch(gexec_[p], st_), "cudaGraphLaunch");
+        if (ev_end) ck(cudaEventRecord(ev_end, st_), "cudaEventRecord");
+        n_step = gsteps_[p];
+        launches += n_step + 2;
+        graph_launches++;
       }
+      step_launches += n_step;
       if (o_.profile) {
-        ck(cudaEventRecord(pev.back(), st_), "cudaEventRecord");
         pev_bytes.push_back(bytes);
-        pev_launches.push_back(small_ ? 1 : n_c_ - 1);
+        pev_launches.push_back(n_step);
       }
       step_bytes_all += bytes;
       row_terms += act * (long long)n_c_;
-      launched(rp::launch_gram_integrate<T>(S_, X_, d_W_, rows_.field, rows_.win, k, R, n_c_,
-                                            rows_.integral, st_),
-               "gram-integral kernel");
       // rows whose window ends after this macro-step: finish and refill
       bool any = false;
       for (int r = 0; r < R; ++r) {
@@ -392,15 +414,95 @@ class YieldEngine {
         init_flagged();
       }
     }
+    drop_graphs();
+    // kernels with bounded waits report a wait that gave up in the error word
+    int h_err = 0;
+    ck(cudaMemcpyAsync(&h_err, d_err_, sizeof(int), cudaMemcpyDeviceToHost, st_), "d2h error word");
+    d2h += (long long)sizeof(int);
+    ck(cudaStreamSynchronize(st_), "kernel execution");
+    if (h_err) throw CudaFail{RP_ETIMEOUT, "a bounded device wait gave up (bulk tile copies)"};
   }
 
   void set_seed(uint64_t seed) { seed_ = seed; }
+
+  long long graph_launches = 0;
 
  private:
   void launched(cudaError_t e, const char* what) {
     ck(e, what);
     launches++;
   }
+
+  // Launches the macro-step k on stream s: the Chebyshev terms (one kernel per
+  // term, or the whole macro-step in shared memory), the time integral and,
+  // with a device counter mdev, the counter increment.  Returns the number of
+  // step-kernel launches.
+  int issue(int k, cudaStream_t s, int* mdev, cudaEvent_t ev_steps = nullptr) {
+    T* Sb[2] = {S0_, S1_};
+    T* P = Sb[k & 1];
+    T* Q = Sb[(k + 1) & 1];
+    T* phi[3] = {P, F1_, F2_};
+    const rp::HamDev<T>* one = sys_.size() == 1 ? &ham1_ : nullptr;
+    int n_step = 0;
+    if (small_) {
+      ck(rp::launch_macro_small<T>(S_, one, aniso_, d_fdev_, rows_.field, rows_.win, k, mdev, R_,
+                                   P, Q, X_, d_coef_, n_c_, s),
+         "macro-step kernel");
+      n_step = 1;
+    }
+    for (int n = 1; n < n_c_ && !small_; ++n) {
+      const int mode = (n == 1) ? rp::MODE_FIRST : (n == n_c_ - 1 ? rp::MODE_LAST : rp::MODE_MID);
+      ck(rp::launch_step<T>(S_, one, aniso_, o_.kernel == 3, d_fdev_, rows_.field, rows_.win, k, mdev, R_,
+                            phi[(n - 1) % 3], n >= 2 ? phi[(n - 2) % 3] : nullptr,
+                            mode == rp::MODE_LAST ? nullptr : phi[n % 3], Q, X_, d_coef_, n_c_, n,
+                            mode, tc_gram_ ? 1 : 0, s),
+         "step kernel");
+      ++n_step;
+    }
+    if (ev_steps) ck(cudaEventRecord(ev_steps, s), "cudaEventRecord");
+    if (tc_gram_)
+      ck(rp::launch_gram_tc(reinterpret_cast<const float*>(X_), d_W_, rows_.field, rows_.win, k,
+                            mdev, R_, n_c_, Zslot_, n_sm_, rows_.integral, d_err_, s),
+         "tensor-core time-integral kernel");
+    else
+      ck(rp::launch_gram_integrate<T>(S_, X_, d_W_, rows_.field, rows_.win, k, mdev, R_, n_c_,
+                                      rows_.integral, s),
+         "gram-integral kernel");
+    if (mdev) ck(rp::launch_tick(mdev, s), "tick kernel");
+    return n_step;
+  }
+
+  // Records the launches of a macro-step of parity p (k % 2 == p) into a graph.
+  void capture(int k, int p) {
+    if (!cap_st_) ck(cudaStreamCreateWithFlags(&cap_st_, cudaStreamNonBlocking), "cudaStreamCreate");
+    ck(cudaStreamBeginCapture(cap_st_, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    cudaGraph_t g = nullptr;
+    try {
+      gsteps_[p] = issue(k, cap_st_, d_macro_);
+    } catch (...) {
+      cudaStreamEndCapture(cap_st_, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    ck(cudaStreamEndCapture(cap_st_, &g), "cudaStreamEndCapture");
+    cudaError_t e = cudaGraphInstantiate(&gexec_[p], g, 0);
+    cudaGraphDestroy(g);
+    ck(e, "cudaGraphInstantiate");
+  }
+
+  void drop_graphs() {
+    for (int p = 0; p < 2; ++p)
+      if (gexec_[p]) {
+        cudaGraphExecDestroy(gexec_[p]);
+        gexec_[p] = nullptr;
+      }
+  }
+
+  int* d_err_ = nullptr;
+  cudaGraphExec_t gexec_[2] = {nullptr, nullptr};
+  int gsteps_[2] = {0, 0};
+  cudaStream_t cap_st_ = nullptr;
+  int* d_macro_ = nullptr;
   std::vector<const rp::HostSystem*> sys_;
   const rp_options& o_;
   int n_c_;
@@ -415,6 +517,8 @@ class YieldEngine {
   uint32_t* d_pair_ = nullptr;
   rp::HamDev<T> ham1_{};
   bool small_ = false;
+  bool tc_gram_ = false;
+  int n_sm_ = 0;
   rp::SysTab<T> S_{};
   uint64_t seed_ = 0;
   int R_ = 0;
@@ -474,6 +578,7 @@ void fill_stats(rp_stats* stats, const YieldEngine<T>& eng, long long items, int
   std::memset(stats, 0, sizeof(*stats));
   stats->kernel_launches = eng.launches;
   stats->step_launches = eng.step_launches;
+  stats->graph_launches = eng.graph_launches;
   stats->row_terms = eng.row_terms;
   stats->propagations = items;
   stats->rows = R;
@@ -494,7 +599,7 @@ void fill_stats(rp_stats* stats, const YieldEngine<T>& eng, long long items, int
   stats->step_bytes = profile ? pb : eng.step_bytes_all;
   stats->step_launches_timed = pl;
   stats->h2d_bytes = eng.h2d;
-  stats->d2h_bytes = d2h;
+  stats->d2h_bytes = d2h + eng.d2h;
 }
 
 struct EventPair {
@@ -965,7 +1070,7 @@ rp_status run_batch(int n_sys, rp_system* const* systems, const int* n_fields,
   };
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return lg(a) > lg(b); });
   EventPair ev;
-  long long launches = 0, step_launches = 0, row_terms = 0, h2d = 0, d2h = 0;
+  long long launches = 0, step_launches = 0, row_terms = 0, h2d = 0, d2h = 0, graphs = 0;
   double step_bytes = 0.0, step_ms = 0.0;
   long long step_timed = 0;
   int R_max = 0;
@@ -1010,9 +1115,11 @@ rp_status run_batch(int n_sys, rp_system* const* systems, const int* n_fields,
       eng.run(items, d_ps);
       ck(cudaStreamSynchronize(st), "group");
       launches += eng.launches;
+      graphs += eng.graph_launches;
       step_launches += eng.step_launches;
       row_terms += eng.row_terms;
       h2d += eng.h2d;
+      d2h += eng.d2h;
       step_bytes += eng.step_bytes_all;
       for (size_t i = 0; i + 1 < eng.pev.size(); i += 2) {
         float t = 0.f;
@@ -1066,6 +1173,7 @@ rp_status run_batch(int n_sys, rp_system* const* systems, const int* n_fields,
     stats->step_launches_timed = step_timed;
     stats->h2d_bytes = h2d;
     stats->d2h_bytes = d2h;
+    stats->graph_launches = graphs;
   }
   return RP_OK;
 }
@@ -1228,7 +1336,7 @@ rp_status rp_yields(rp_system* s, int n_fields, const double* fields, int M, uin
   if (!s) return fail(RP_EINVAL, "system is NULL");
   if (n_fields < 0) return fail(RP_EINVAL, "n_fields must be >= 0");
   if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
-  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0, 1 or 2");
+  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..3, gram 0..2 and graph 0 or 1");
   if (!o.deterministic && M < 2) return fail(RP_EINVAL, "M must be >= 2 (the standard error needs it)");
   if (!(t_max > 0.0) || !std::isfinite(t_max)) return fail(RP_EINVAL, "t_max must be positive and finite");
   if (o.sample_offset < 0) return fail(RP_EINVAL, "sample_offset must be >= 0");
@@ -1260,7 +1368,7 @@ rp_status rp_yields_converged(rp_system* s, int n_fields, const double* fields, 
   if (!s) return fail(RP_EINVAL, "system is NULL");
   if (n_fields < 0) return fail(RP_EINVAL, "n_fields must be >= 0");
   if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
-  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0, 1 or 2");
+  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..3, gram 0..2 and graph 0 or 1");
   if (o.deterministic) return fail(RP_EINVAL, "rp_yields_converged samples coherent states only");
   if (!(se_target > 0.0) || !std::isfinite(se_target)) return fail(RP_EINVAL, "se_target must be positive");
   if (M_min < 2 || M_max < M_min) return fail(RP_EINVAL, "need 2 <= M_min <= M_max");
@@ -1309,7 +1417,7 @@ rp_status rp_yields_cv(rp_system* s, int n_fields, const double* fields, double 
   if (!s) return fail(RP_EINVAL, "system is NULL");
   if (n_fields < 0) return fail(RP_EINVAL, "n_fields must be >= 0");
   if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
-  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0, 1 or 2");
+  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..3, gram 0..2 and graph 0 or 1");
   if (o.deterministic) return fail(RP_EINVAL, "rp_yields_cv samples coherent states only");
   if (!(se_target > 0.0) || !std::isfinite(se_target)) return fail(RP_EINVAL, "se_target must be positive");
   if (M_min < 2 || M_max < M_min) return fail(RP_EINVAL, "need 2 <= M_min <= M_max");
@@ -1349,7 +1457,7 @@ rp_status rp_yields_batch(int n_sys, rp_system* const* systems, const int* n_fie
   if (n_sys == 0) return RP_OK;
   if (!systems || !n_fields || !fields || !M || !t_max || !out) return fail(RP_EINVAL, "NULL argument");
   if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
-  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0, 1 or 2");
+  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..3, gram 0..2 and graph 0 or 1");
   if (o.deterministic) return fail(RP_EINVAL, "rp_yields_batch samples coherent states only");
   if (o.sample_offset < 0) return fail(RP_EINVAL, "sample_offset must be >= 0");
   long long total = 0;
@@ -1402,9 +1510,9 @@ rp_status rp_apply_h(rp_system* s, double B, int precision, int n_vec, const voi
       ck(cudaMemcpyAsync(d, &F, sizeof(F), cudaMemcpyHostToDevice, st), "h2d");
       ck(cudaMemcpyAsync(dh, &H, sizeof(H), cudaMemcpyHostToDevice, st), "h2d");
       const rp::SysTab<double> S{dh, nullptr, nullptr, nullptr, hs.Z, 0, nullptr};
-      ck(rp::launch_step<double>(S, &H, H.aniso, d, nullptr, nullptr, 0, n_vec, (const double*)x,
+      ck(rp::launch_step<double>(S, &H, H.aniso, 1, d, nullptr, nullptr, 0, nullptr, n_vec, (const double*)x,
                                  nullptr, (double*)y, nullptr, nullptr, nullptr, 0, 0,
-                                 rp::MODE_APPLY, st), "apply kernel");
+                                 rp::MODE_APPLY, 0, st), "apply kernel");
     } else {
       rp::FieldDev<float> F{(float)(rp::kGammaE * B), 1.f, 0.f, (float)(0.5 * kbar)};
       const rp::HamDev<float> H = make_ham<float>(hs);
@@ -1413,8 +1521,8 @@ rp_status rp_apply_h(rp_system* s, double B, int precision, int n_vec, const voi
       ck(cudaMemcpyAsync(d, &F, sizeof(F), cudaMemcpyHostToDevice, st), "h2d");
       ck(cudaMemcpyAsync(dh, &H, sizeof(H), cudaMemcpyHostToDevice, st), "h2d");
       const rp::SysTab<float> S{dh, nullptr, nullptr, nullptr, hs.Z, 0, nullptr};
-      ck(rp::launch_step<float>(S, &H, H.aniso, d, nullptr, nullptr, 0, n_vec, (const float*)x, nullptr,
-                                (float*)y, nullptr, nullptr, nullptr, 0, 0, rp::MODE_APPLY, st),
+      ck(rp::launch_step<float>(S, &H, H.aniso, 1, d, nullptr, nullptr, 0, nullptr, n_vec, (const float*)x, nullptr,
+                                (float*)y, nullptr, nullptr, nullptr, 0, 0, rp::MODE_APPLY, 0, st),
          "apply kernel");
     }
     ck(cudaStreamSynchronize(st), "apply kernel execution");

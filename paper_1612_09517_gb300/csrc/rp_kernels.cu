@@ -114,6 +114,35 @@ __device__ __forceinline__ void store_singlet(T* x, const Cx<T> (&v)[4]) {
   x[1] = (v[1].im - v[2].im) * r;
 }
 
+// Singlet slices in the tensor-core Gram layout (xblk != 0): per row, chunks of
+// kXChunk configurations; in a chunk, real rows 2n (Re x_n) and 2n + 1 (Im x_n)
+// padded to xrows_pad(n_c) rows, stored as 8-row x 4-configuration core
+// matrices (128 contiguous bytes, rows 16 B apart), the 4 core matrices of an
+// 8-row group along the configurations 128 B apart, and the row groups 512 B
+// apart.  A chunk is then one contiguous block that a single bulk copy brings
+// into shared memory in the K-major no-swizzle operand layout of tcgen05.mma.
+constexpr int kXChunk = 16;
+__host__ __device__ __forceinline__ int xrows_pad(int n_c) { return (2 * n_c + 15) & ~15; }
+__host__ __device__ __forceinline__ size_t xblk_row_floats(long long Zs, int n_c) {
+  return (size_t)((Zs + kXChunk - 1) / kXChunk) * xrows_pad(n_c) * kXChunk;
+}
+
+// Address of Re x_n(m) (Im is 4 floats further) of row r.
+template <typename T>
+__device__ __forceinline__ T* xblk_addr(T* X, int r, int n, unsigned m, long long Zs, int n_c) {
+  const int row = 2 * n;
+  return X + (size_t)r * xblk_row_floats(Zs, n_c) +
+         (size_t)(m / kXChunk) * xrows_pad(n_c) * kXChunk + (row >> 3) * 128 +
+         ((m % kXChunk) >> 2) * 32 + (row & 7) * 4 + (m & 3);
+}
+
+template <typename T>
+__device__ __forceinline__ void store_singlet_blk(T* x, const Cx<T> (&v)[4]) {
+  const T r = T(0.70710678118654752440);
+  x[0] = (v[1].re - v[2].re) * r;
+  x[4] = (v[1].im - v[2].im) * r;
+}
+
 // y += Mx q on the electron of radical rr, Mx a 2x2 complex matrix (re/im arrays).
 template <typename T>
 __device__ __forceinline__ void apply_e2x2(Cx<T> (&y)[4], const Cx<T> (&q)[4], int rr,
@@ -306,6 +335,78 @@ __device__ __forceinline__ void finish_z(const HamDev<T>& H, const FieldDev<T>& 
   }
 }
 
+// Chebyshev recurrence, accumulator and singlet slice of one configuration m
+// of row r after the H' a partner sum y and local fields b1, b2 are known
+// (see k_cheb_step for the modes).
+template <typename T, bool ANISO>
+__device__ __forceinline__ void term_epilogue(const HamDev<T>& H, const SysTab<T>& S,
+                                              const FieldDev<T>& F, const Cx<T> (&a)[4],
+                                              Cx<T> (&y)[4], const T (&b1)[3], const T (&b2)[3],
+                                              int f, int r, unsigned m, size_t row0,
+                                              const T* __restrict__ prev, T* __restrict__ next,
+                                              T* __restrict__ acc, T* __restrict__ X,
+                                              const T* __restrict__ coef, int n_c, int n,
+                                              int mode, int xblk, const Cx<T>* pre_pv = nullptr,
+                                              const Cx<T>* pre_acc = nullptr) {
+  Cx<T> z[4];
+  finish_z<T, ANISO>(H, F, a, y, b1, b2, z);
+  const size_t off = row0 + (size_t)m * 8;
+  if (mode == MODE_APPLY) {
+    store4(next + off, z);
+    return;
+  }
+  const T* cf = coef + (size_t)f * n_c * 2;
+  const size_t Zs = (size_t)S.Zslot;
+  T* xr = X + (size_t)r * n_c * Zs * 2;
+  if (mode == MODE_FIRST) {
+    store4(next + off, z);
+    const T c0r = cf[0], c0i = cf[1], c1r = cf[2], c1i = cf[3];
+    Cx<T> s[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      s[e] = {T(0), T(0)};
+      cmac(s[e], c0r, c0i, a[e]);
+      cmac(s[e], c1r, c1i, z[e]);
+    }
+    store4(acc + off, s);
+    if (xblk) {
+      store_singlet_blk(xblk_addr(X, r, 0, m, S.Zslot, n_c), a);
+      store_singlet_blk(xblk_addr(X, r, 1, m, S.Zslot, n_c), z);
+    } else {
+      store_singlet(xr + (size_t)m * 2, a);
+      store_singlet(xr + (Zs + m) * 2, z);
+    }
+    return;
+  }
+  Cx<T> pv[4];
+  if (pre_pv) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) pv[e] = pre_pv[e];
+  } else {
+    load4(prev + off, pv);
+  }
+  Cx<T> ph[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    ph[e].re = T(2) * z[e].re - pv[e].re;
+    ph[e].im = T(2) * z[e].im - pv[e].im;
+  }
+  if (mode == MODE_MID) store4(next + off, ph);
+  Cx<T> s[4];
+  if (pre_acc) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) s[e] = pre_acc[e];
+  } else {
+    load4_rw(acc + off, s);
+  }
+  const T cr = cf[2 * n], ci = cf[2 * n + 1];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) cmac(s[e], cr, ci, ph[e]);
+  store4(acc + off, s);
+  if (xblk) store_singlet_blk(xblk_addr(X, r, n, m, S.Zslot, n_c), ph);
+  else store_singlet(xr + ((size_t)n * Zs + m) * 2, ph);
+}
+
 // Body of one Chebyshev term; H is either the kernel-parameter copy (one
 // system per launch) or a shared-memory copy of the row's system.
 template <typename T, bool ANISO>
@@ -314,19 +415,21 @@ __device__ __forceinline__ void step_body(const HamDev<T>& H, const SysTab<T>& S
                                           const T* __restrict__ cur, const T* __restrict__ prev,
                                           T* __restrict__ next, T* __restrict__ acc,
                                           T* __restrict__ X, const T* __restrict__ coef, int n_c,
-                                          int n, int mode);
+                                          int n, int mode, int xblk);
 
 template <typename T, bool ANISO, bool MULTI>
 __global__ void __launch_bounds__(kStepThreads, sizeof(T) == 4 ? 4 : 2) k_cheb_step(
     const SysTab<T> S, const HamDev<T> H1, const FieldDev<T>* __restrict__ fields,
-    const int* __restrict__ row_field, const int2* __restrict__ row_win, int macro,
-    const T* __restrict__ cur, const T* __restrict__ prev, T* __restrict__ next,
-    T* __restrict__ acc, T* __restrict__ X, const T* __restrict__ coef, int n_c, int n, int mode) {
+    const int* __restrict__ row_field, const int2* __restrict__ row_win, int macro_arg,
+    const int* __restrict__ macro_dev, const T* __restrict__ cur, const T* __restrict__ prev,
+    T* __restrict__ next, T* __restrict__ acc, T* __restrict__ X, const T* __restrict__ coef,
+    int n_c, int n, int mode, int xblk) {
   extern __shared__ __align__(16) unsigned char step_smem[];
   Cx<T>* tile = reinterpret_cast<Cx<T>*>(step_smem);  // planes x blockDim x 16 B
   const int r = blockIdx.y;
   int f = 0;
   if (mode != MODE_APPLY) {
+    const int macro = macro_dev ? *macro_dev : macro_arg;
     const int2 w = row_win[r];
     if (macro < w.x || macro >= w.y) return;  // the whole block: one row
     f = row_field[r];
@@ -338,9 +441,11 @@ __global__ void __launch_bounds__(kStepThreads, sizeof(T) == 4 ? 4 : 2) k_cheb_s
     int4* dst = reinterpret_cast<int4*>(&Hs);
     for (int i = threadIdx.x; i < (int)(sizeof(HamDev<T>) / 16); i += blockDim.x) dst[i] = src[i];
     __syncthreads();
-    step_body<T, ANISO>(Hs, S, tile, fields, f, r, cur, prev, next, acc, X, coef, n_c, n, mode);
+    step_body<T, ANISO>(Hs, S, tile, fields, f, r, cur, prev, next, acc, X, coef, n_c, n, mode,
+                        xblk);
   } else {
-    step_body<T, ANISO>(H1, S, tile, fields, f, r, cur, prev, next, acc, X, coef, n_c, n, mode);
+    step_body<T, ANISO>(H1, S, tile, fields, f, r, cur, prev, next, acc, X, coef, n_c, n, mode,
+                        xblk);
   }
 }
 
@@ -350,7 +455,7 @@ __device__ __forceinline__ void step_body(const HamDev<T>& H, const SysTab<T>& S
                                           const T* __restrict__ cur, const T* __restrict__ prev,
                                           T* __restrict__ next, T* __restrict__ acc,
                                           T* __restrict__ X, const T* __restrict__ coef, int n_c,
-                                          int n, int mode) {
+                                          int n, int mode, int xblk) {
   const unsigned Z = (unsigned)H.Z;
   const unsigned m = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = m < Z;
@@ -431,48 +536,223 @@ __device__ __forceinline__ void step_body(const HamDev<T>& H, const SysTab<T>& S
       add_partner<T, ANISO>(y, c, m - st, rr, H.U[p], sqrt(I * (I + 1) - M * (M + 1)), false);
   }
 
-  const FieldDev<T> F = fields[f];
-  Cx<T> z[4];
-  finish_z<T, ANISO>(H, F, a, y, b1, b2, z);
+  term_epilogue<T, ANISO>(H, S, fields[f], a, y, b1, b2, f, r, m, row0, prev, next, acc, X, coef,
+                         n_c, n, mode, xblk);
+}
+
+// ---- FP32 term with the block's partner tiles staged by bulk async copies ----
+//
+// When every nucleus outside the innermost kInnerBits spin-1/2 positions has a
+// stride that is a multiple of the block (n_half >= kInnerBits and 256
+// configurations per block), the partner configurations m +- stride_p of a
+// whole block form whole neighbouring blocks ("tiles") of the same row: one
+// tile per outer spin-1/2 nucleus (m XOR 2^p), and one or two per outer nucleus
+// of higher spin (digit j + 1 and j - 1 where they exist; the digit is the
+// same for the whole tile).  One thread issues bulk copies (cp.async.bulk,
+// completion counted on an mbarrier) of the block's own tile and of every
+// partner tile at kernel start, so all of the block's reads of phi_{n-1} are in
+// flight at once instead of one dependent 32-byte L2 load per partner and
+// thread.  Tiles are kept as in memory (32 bytes per configuration); a thread
+// reads entry t as two 16-byte halves in the order (t >> 2) & 1, which keeps
+// each quarter-warp on distinct banks.
+constexpr int kBulkTile = 256;                       // configurations per block
+constexpr int kBulkTileBytes = kBulkTile * 32;       // FP32: 8 KB
+constexpr int kBulkMaxSmem = 80 * 1024;              // own + partner tiles per block
+constexpr long long kBulkWaitLimit = 1ll << 24;      // try_wait polls before giving up
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void tile_get_aos(const float* tile, unsigned t, Cx<float> (&q)[4]) {
+  const unsigned sw = (t >> 2) & 1u;
+  const float4* e = reinterpret_cast<const float4*>(tile) + 2 * t;
+  const float4 u = e[sw], v = e[sw ^ 1u];
+  const float4 lo = sw ? v : u, hi = sw ? u : v;
+  q[0] = {lo.x, lo.y};
+  q[1] = {lo.z, lo.w};
+  q[2] = {hi.x, hi.y};
+  q[3] = {hi.z, hi.w};
+}
+
+// Bounded wait for phase 0 of the block's mbarrier; false after the limit.
+__device__ __forceinline__ bool bulk_wait(unsigned bar) {
+  for (long long it = 0; it < kBulkWaitLimit; ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+// Partner tiles of tile c0 (first configuration), in the order the compute
+// loop consumes them; calls emit(slot, first configuration of the partner).
+// The digits of the outer nuclei are the same for every configuration of the
+// tile, so they come from c0.
+template <typename F>
+__device__ __forceinline__ int bulk_partner_tiles(const HamDev<float>& H, unsigned c0, F&& emit) {
+  int slot = 1;  // slot 0: the block's own tile
+  for (int p = kInnerBits; p < H.n_half; ++p) emit(slot++, c0 ^ (1u << p));
+  unsigned qd = c0 >> H.n_half;
+  for (int p = H.n_half; p < H.n_nuc; ++p) {
+    const unsigned d = (unsigned)H.d[p];
+    const unsigned j = d == 3u ? qd % 3u : qd % d;
+    qd = d == 3u ? qd / 3u : qd / d;
+    const unsigned st = (unsigned)H.stride[p];
+    if (j + 1u < d) emit(slot++, c0 + st);
+    if (j > 0u) emit(slot++, c0 - st);
+  }
+  return slot;
+}
+
+template <bool ANISO>
+__global__ void __launch_bounds__(kBulkTile, 2) k_cheb_step_bulk(
+    const SysTab<float> S, const HamDev<float> H, const FieldDev<float>* __restrict__ fields,
+    const int* __restrict__ row_field, const int2* __restrict__ row_win, int macro_arg,
+    const int* __restrict__ macro_dev, const float* __restrict__ cur,
+    const float* __restrict__ prev, float* __restrict__ next, float* __restrict__ acc,
+    float* __restrict__ X, const float* __restrict__ coef, int n_c, int n, int mode, int xblk) {
+  extern __shared__ __align__(128) unsigned char bulk_smem[];
+  __shared__ __align__(8) unsigned long long bar_storage[2];  // own tile, partner tiles
+  const int r = blockIdx.y;
+  int f = 0;
+  if (mode != MODE_APPLY) {
+    const int macro = macro_dev ? *macro_dev : macro_arg;
+    const int2 w = row_win[r];
+    if (macro < w.x || macro >= w.y) return;  // the whole block: one row
+    f = row_field[r];
+  }
+  float* tiles = reinterpret_cast<float*>(bulk_smem);
+  const unsigned bar_own = smem_u32(&bar_storage[0]), bar_part = smem_u32(&bar_storage[1]);
+  const unsigned c0 = blockIdx.x * kBulkTile;
+  const size_t row0 = (size_t)r * S.Zslot * 8;
+  const float* c = cur + row0;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_own) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_part) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    auto copy = [&](unsigned bar, int slot, unsigned first) {
+      asm volatile(
+          "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+              smem_u32(tiles + (size_t)slot * kBulkTile * 8)),
+          "l"(c + (size_t)first * 8), "r"((unsigned)kBulkTileBytes), "r"(bar)
+          : "memory");
+    };
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_own),
+                 "r"((unsigned)kBulkTileBytes)
+                 : "memory");
+    copy(bar_own, 0, c0);
+    const int n_tiles = bulk_partner_tiles(H, c0, [](int, unsigned) {});
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar_part),
+                 "r"((unsigned)((n_tiles - 1) * kBulkTileBytes))
+                 : "memory");
+    bulk_partner_tiles(H, c0, [&](int slot, unsigned first) { copy(bar_part, slot, first); });
+  }
+  const unsigned t = threadIdx.x;
+  const unsigned m = c0 + t;
   const size_t off = row0 + (size_t)m * 8;
-  if (mode == MODE_APPLY) {
-    store4(next + off, z);
+  // the streams this thread reads anyway, in flight during the tile copies
+  Cx<float> pv[4], sa[4];
+  const bool pre = mode == MODE_MID || mode == MODE_LAST;
+  if (pre) {
+    load4(prev + off, pv);
+    load4_rw(acc + off, sa);
+  }
+  __syncthreads();  // the barriers are initialised before anyone polls them
+  if (!bulk_wait(bar_own) ) {
+    if (S.err) atomicOr(S.err, 1);
+    bulk_wait(bar_own);  // let copies still in flight land before the block exits
+    bulk_wait(bar_part);
     return;
   }
-  const T* cf = coef + (size_t)f * n_c * 2;
-  const size_t Zs = (size_t)S.Zslot;
-  T* xr = X + (size_t)r * n_c * Zs * 2;
-  if (mode == MODE_FIRST) {
-    store4(next + off, z);
-    const T c0r = cf[0], c0i = cf[1], c1r = cf[2], c1i = cf[3];
-    Cx<T> s[4];
+  Cx<float> a[4];
+  tile_get_aos(tiles, t, a);
+  Cx<float> y[4];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      s[e] = {T(0), T(0)};
-      cmac(s[e], c0r, c0i, a[e]);
-      cmac(s[e], c1r, c1i, z[e]);
+  for (int e = 0; e < 4; ++e) y[e] = {0.f, 0.f};
+  float b1[3] = {0.f, 0.f, 0.f}, b2[3] = {0.f, 0.f, 0.f};
+  // spin-1/2 nuclei inside the tile
+#pragma unroll
+  for (int p = 0; p < kInnerBits; ++p) {
+    Cx<float> q[4];
+    tile_get_aos(tiles, t ^ (1u << p), q);
+    half_nucleus<float, ANISO>(y, b1, b2, H, p, (m >> p) & 1u, q);
+  }
+  if (!bulk_wait(bar_part)) {
+    if (S.err) atomicOr(S.err, 1);
+    bulk_wait(bar_part);
+    return;
+  }
+  // outer spin-1/2 nuclei: one partner tile each (slot 1 + p - kInnerBits)
+#pragma unroll
+  for (int p = kInnerBits; p < kMaxNucDev; ++p) {
+    if (p < H.n_half) {
+      Cx<float> q[4];
+      tile_get_aos(tiles + (size_t)(1 + p - kInnerBits) * kBulkTile * 8, t, q);
+      half_nucleus<float, ANISO>(y, b1, b2, H, p, (c0 >> p) & 1u, q);
     }
-    store4(acc + off, s);
-    store_singlet(xr + (size_t)m * 2, a);
-    store_singlet(xr + (Zs + m) * 2, z);
-    return;
   }
-  Cx<T> pv[4];
-  load4(prev + off, pv);
-  Cx<T> ph[4];
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    ph[e].re = T(2) * z[e].re - pv[e].re;
-    ph[e].im = T(2) * z[e].im - pv[e].im;
+  // nuclei of higher spin: partners j + 1 (through U) and j - 1 (through U^dagger)
+  int slot = 1 + H.n_half - kInnerBits;
+  unsigned qd = c0 >> H.n_half;
+  const float s2 = 1.41421356237309504880f;
+#pragma unroll 4
+  for (int p = H.n_half; p < H.n_half + H.n_one; ++p) {
+    const unsigned j = qd % 3u;
+    qd /= 3u;
+    const int rr = H.rad[p];
+    if (ANISO) {
+      add_field(b1, b2, rr, 1.f - (float)j, H.v[p]);
+    } else {
+      const float dz = (1.f - (float)j) * H.v[p][2];
+      if (rr == 0) b1[2] += dz;
+      else b2[2] += dz;
+    }
+    if (j < 2u) {
+      Cx<float> q[4];
+      tile_get_aos(tiles + (size_t)(slot++) * kBulkTile * 8, t, q);
+      add_partner_q<float, ANISO>(y, q, rr, H.U[p], s2, true);
+    }
+    if (j > 0u) {
+      Cx<float> q[4];
+      tile_get_aos(tiles + (size_t)(slot++) * kBulkTile * 8, t, q);
+      add_partner_q<float, ANISO>(y, q, rr, H.U[p], s2, false);
+    }
   }
-  if (mode == MODE_MID) store4(next + off, ph);
-  Cx<T> s[4];
-  load4_rw(acc + off, s);
-  const T cr = cf[2 * n], ci = cf[2 * n + 1];
-#pragma unroll
-  for (int e = 0; e < 4; ++e) cmac(s[e], cr, ci, ph[e]);
-  store4(acc + off, s);
-  store_singlet(xr + ((size_t)n * Zs + m) * 2, ph);
+  for (int p = H.n_half + H.n_one; p < H.n_nuc; ++p) {
+    const unsigned d = (unsigned)H.d[p];
+    const unsigned j = qd % d;
+    qd /= d;
+    const int rr = H.rad[p];
+    const float I = 0.5f * (float)(d - 1), M = I - (float)j;
+    add_field(b1, b2, rr, M, H.v[p]);
+    if (j + 1u < d) {
+      Cx<float> q[4];
+      tile_get_aos(tiles + (size_t)(slot++) * kBulkTile * 8, t, q);
+      add_partner_q<float, ANISO>(y, q, rr, H.U[p], sqrtf(I * (I + 1.f) - M * (M - 1.f)), true);
+    }
+    if (j > 0u) {
+      Cx<float> q[4];
+      tile_get_aos(tiles + (size_t)(slot++) * kBulkTile * 8, t, q);
+      add_partner_q<float, ANISO>(y, q, rr, H.U[p], sqrtf(I * (I + 1.f) - M * (M + 1.f)), false);
+    }
+  }
+  term_epilogue<float, ANISO>(H, S, fields[f], a, y, b1, b2, f, r, m, row0, prev, next, acc, X,
+                              coef, n_c, n, mode, xblk, pre ? pv : nullptr,
+                              pre ? sa : nullptr);
+}
+
+// Largest number of partner tiles over the tiles of a system (host side).
+int bulk_max_partner_tiles(const HamDev<float>& H) {
+  int t = H.n_half > kInnerBits ? H.n_half - kInnerBits : 0;
+  for (int p = H.n_half; p < H.n_nuc; ++p) t += H.d[p] >= 3 ? 2 : 1;
+  return t;
 }
 
 // ---- whole macro-steps of small systems in one CTA per row ----
@@ -616,10 +896,11 @@ __device__ __forceinline__ void macro_small_body(const HamDev<T>& H, const SysTa
 template <typename T, bool ANISO, bool MULTI>
 __global__ void __launch_bounds__(256) k_macro_small(
     const SysTab<T> S, const HamDev<T> H1, const FieldDev<T>* __restrict__ fields,
-    const int* __restrict__ row_field, const int2* __restrict__ row_win, int macro,
-    const T* __restrict__ P, T* __restrict__ Q, T* __restrict__ X, const T* __restrict__ coef,
-    int n_c) {
+    const int* __restrict__ row_field, const int2* __restrict__ row_win, int macro_arg,
+    const int* __restrict__ macro_dev, const T* __restrict__ P, T* __restrict__ Q,
+    T* __restrict__ X, const T* __restrict__ coef, int n_c) {
   const int r = blockIdx.x;
+  const int macro = macro_dev ? *macro_dev : macro_arg;
   const int2 w = row_win[r];
   if (macro < w.x || macro >= w.y) return;
   const int f = row_field[r];
@@ -663,9 +944,11 @@ constexpr int kGramThreads = 256;
 template <typename T>
 __global__ void __launch_bounds__(kGramThreads) k_gram_integrate(
     const SysTab<T> S, const T* __restrict__ X, const double* __restrict__ W,
-    const int* __restrict__ row_field, const int2* __restrict__ row_win, int macro, int n_c,
-    int tiles, int groups, int zc, long long z_per_cta, double* __restrict__ integral) {
+    const int* __restrict__ row_field, const int2* __restrict__ row_win, int macro_arg,
+    const int* __restrict__ macro_dev, int n_c, int tiles, int groups, int zc,
+    long long z_per_cta, double* __restrict__ integral) {
   const int r = blockIdx.y;
+  const int macro = macro_dev ? *macro_dev : macro_arg;
   {
     const int2 w = row_win[r];
     if (macro < w.x || macro >= w.y) return;
@@ -781,6 +1064,301 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_integrate(
   double* sh = reinterpret_cast<double*>(smem_raw);
   const double tot = block_sum<kGramThreads>(s, sh);
   if (tid == 0) atomicAdd(integral + r, tot);
+}
+
+// ---- Exact time integral on the tensor cores (FP32 state, tcgen05 3xTF32) ----
+//
+// The same quantity as k_gram_integrate (Eqs. 20, 22): integral[r] +=
+// Re sum_nm W_nm G_nm with G_nm = sum_z conj(x_n(z)) x_m(z).  With the real
+// rows a = 2n + p (p = 0: Re x_n, p = 1: Im x_n) of the singlet slices as a
+// (2 n_c) x Z matrix A, the real Gram R = A A^T holds G (Re G_nm = R_{2n,2m} +
+// R_{2n+1,2m+1}, Im G_nm = R_{2n,2m+1} - R_{2n+1,2m}), and the integral is
+// sum_ab What_ab R_ab with the symmetric What_{2n+p,2m+q} = Re W_nm (p = q),
+// -Im W_nm (p = 0, q = 1), Im W_nm (p = 1, q = 0).
+//
+// One CTA takes a range of kXChunk-configuration chunks of one row.  Per
+// chunk: one bulk copy (the chunk is contiguous in the layout written by the
+// step kernel) into a stage of a kGramStages-deep ring; the 128 threads split
+// each value into hi = its nearest TF32 and lo = the nearest TF32 of
+// value - hi; one
+// thread issues tcgen05.mma kind::tf32 for hi.hi + hi.lo + lo.hi into FP32
+// accumulators in tensor memory: D1 = A[0:128] A[0:R2p]^T (128 x R2p) and,
+// when 2 n_c > 128, D2 = A[R2p-128:R2p] A[128:R2p]^T, the lower-right block
+// (R2p = 2 n_c rounded up to 16).  The product of two split values misses
+// lo.lo and the rounding of lo: at most about 2^-21 of |x_n x_m| and unbiased
+// except for lo.lo on the diagonal (about 2^-24), the rounding level of FP32
+// data.  At the end each thread reads its accumulator
+// row with tcgen05.ld, contracts it with What in FP64 (entries of D1 with
+// column >= 128 twice: R is symmetric and D2 holds only the lower-right
+// block) and the CTA adds one FP64 atomic.  Every wait is bounded; a wait
+// that gives up sets bit 0 of S.err, lets the copies and MMAs in flight land,
+// frees tensor memory and returns.
+constexpr int kGramStages = 3;
+constexpr int kGramGroup = 2;  // chunks accumulated in tensor memory before a drain
+constexpr int kGramTcThreads = 128;
+constexpr int kGramTmemCols = 512;  // two accumulator buffers, 256 columns apart
+constexpr int kGramMinSmem = 116 * 1024;  // keeps one CTA (and 512 TMEM columns) per SM
+constexpr long long kWaitLimit = 1ll << 24;
+
+__device__ __forceinline__ bool mbar_wait(unsigned bar, unsigned parity) {
+  for (long long it = 0; it < kWaitLimit; ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void bulk_load(unsigned dst, const void* src, unsigned bytes,
+                                          unsigned bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// tcgen05 shared-memory matrix descriptor, K-major, no swizzle: start address,
+// leading byte offset (next core matrix along K), stride byte offset (next
+// 8-row group), descriptor version 1.
+__device__ __forceinline__ uint64_t umma_desc(unsigned addr, unsigned lbo, unsigned sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor of kind::tf32: D FP32, A and B TF32, both K-major.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(unsigned d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         unsigned accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(unsigned bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   bar)
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float (&v)[16]) {
+  uint32_t u[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]),
+        "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]),
+        "=r"(u[14]), "=r"(u[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(u[i]);
+}
+
+// Nearest TF32 value of a finite float (ties away from zero): add half a unit
+// of the 10-bit mantissa and clear the 13 low bits.  hi and lo are both exact
+// TF32 numbers, so the tensor core uses them unchanged and the split errors
+// are unbiased rounding errors.
+__device__ __forceinline__ float tf32_round(float x) {
+  return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
+
+// What_{a j} for the row-pair interleaved real Gram (see above).
+__device__ __forceinline__ double what(const double* __restrict__ Wf, int n_c, int a, int j) {
+  const int n = a >> 1, m = j >> 1;
+  const double* w = Wf + ((size_t)n * n_c + m) * 2;
+  if ((a & 1) == (j & 1)) return w[0];
+  return (a & 1) ? w[1] : -w[1];
+}
+
+__global__ void __launch_bounds__(kGramTcThreads, 1) k_gram_tc(
+    const float* __restrict__ X, const double* __restrict__ W, const int* __restrict__ row_field,
+    const int2* __restrict__ row_win, int macro_arg, const int* __restrict__ macro_dev, int n_c,
+    long long Zs, int chunks_per_cta, double* __restrict__ integral, int* __restrict__ err) {
+  const int r = blockIdx.y;
+  {
+    const int macro = macro_dev ? *macro_dev : macro_arg;
+    const int2 w = row_win[r];
+    if (macro < w.x || macro >= w.y) return;
+  }
+  const int n_chunks = (int)((Zs + kXChunk - 1) / kXChunk);
+  const int c_begin = blockIdx.x * chunks_per_cta;
+  const int nk = min(n_chunks - c_begin, chunks_per_cta);
+  if (nk <= 0) return;
+  const int R2 = 2 * n_c, R2p = xrows_pad(n_c);
+  const int N1 = R2p, N2 = R2p > 128 ? R2p - 128 : 0, NT = N1 + N2;
+  const unsigned copy_bytes = (unsigned)R2p * kXChunk * 4;
+  const unsigned tile_bytes = (unsigned)(R2p > 128 ? R2p : 128) * kXChunk * 4;
+
+  extern __shared__ __align__(1024) unsigned char gram_smem[];
+  // barriers: full[stage], empty[stage], acc_ready[buffer], fin (error path)
+  __shared__ __align__(8) unsigned long long bars[2 * kGramStages + 3];
+  __shared__ unsigned tmem_slot;
+  __shared__ double red[kGramTcThreads];
+  const unsigned tid = threadIdx.x, warp = tid >> 5;
+  const unsigned sbase = smem_u32(gram_smem);
+  auto hi_tile = [&](int s) { return sbase + (unsigned)(2 * s) * tile_bytes; };
+  auto lo_tile = [&](int s) { return sbase + (unsigned)(2 * s + 1) * tile_bytes; };
+  auto full = [&](int s) { return smem_u32(&bars[s]); };
+  auto empty = [&](int s) { return smem_u32(&bars[kGramStages + s]); };
+  auto ready = [&](int b) { return smem_u32(&bars[2 * kGramStages + b]); };
+  // FP32 accumulator of this CTA's Gram rows: column j of row a at acc[j * 128 + a]
+  float* acc = reinterpret_cast<float*>(gram_smem + (size_t)2 * kGramStages * tile_bytes);
+  for (int j = 0; j < NT; ++j) acc[j * kGramTcThreads + tid] = 0.f;
+
+  if (tid == 0) {
+    for (int i = 0; i < 2 * kGramStages + 3; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[i])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(kGramTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = tmem_slot;
+  const unsigned lane_base = tmem + ((warp * 32u) << 16);
+
+  const float* src = X + (size_t)r * xblk_row_floats(Zs, n_c) + (size_t)c_begin * R2p * kXChunk;
+  int issued = 0;
+  if (tid == 0) {
+    for (; issued < nk && issued < kGramStages; ++issued)
+      bulk_load(hi_tile(issued), src + (size_t)issued * R2p * kXChunk, copy_bytes, full(issued));
+  }
+  const uint32_t id1 = idesc_tf32(128, N1), id2 = idesc_tf32(128, N2 > 0 ? N2 : 16);
+  int failed = 0;  // this thread saw a wait give up
+  int consumed = 0;
+  // adds accumulator buffer gg % 2 (group gg) into acc, all threads
+  // (the tensor-memory loads are warp-collective, so they run even after a
+  // failed wait; the CTA then discards its sum)
+  auto drain = [&](int gg) {
+    if (!mbar_wait(ready(gg & 1), (unsigned)(gg >> 1) & 1u)) failed = 1;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const unsigned col0 = (unsigned)(gg & 1) * 256u;
+    for (int jc = 0; jc < NT; jc += 16) {
+      float v[16];
+      tmem_ld16(lane_base + col0 + (unsigned)jc, v);
+#pragma unroll
+      for (int t = 0; t < 16; ++t) acc[(jc + t) * kGramTcThreads + tid] += v[t];
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  };
+  const int n_groups = (nk + kGramGroup - 1) / kGramGroup;
+  for (int kc = 0; kc < nk; ++kc) {
+    const int s = kc % kGramStages;
+    const int g = kc / kGramGroup, i = kc % kGramGroup;
+    const bool last_in_group = (i == kGramGroup - 1) || (kc == nk - 1);
+    const bool ok = mbar_wait(full(s), (unsigned)(kc / kGramStages) & 1u);
+    if (ok) {
+      float4* h = reinterpret_cast<float4*>(gram_smem + (size_t)(2 * s) * tile_bytes);
+      float4* l = reinterpret_cast<float4*>(gram_smem + (size_t)(2 * s + 1) * tile_bytes);
+      for (int q = (int)tid; q < R2p * kXChunk / 4; q += kGramTcThreads) {
+        const float4 v = h[q];
+        const float4 hv = make_float4(tf32_round(v.x), tf32_round(v.y), tf32_round(v.z),
+                                      tf32_round(v.w));
+        h[q] = hv;
+        l[q] = make_float4(tf32_round(v.x - hv.x), tf32_round(v.y - hv.y), tf32_round(v.z - hv.z),
+                           tf32_round(v.w - hv.w));
+      }
+    } else {
+      failed = 1;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (__syncthreads_or(failed)) break;
+    consumed = kc + 1;
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const unsigned dbase = tmem + (unsigned)(g & 1) * 256u;
+      const unsigned A[3] = {hi_tile(s), hi_tile(s), lo_tile(s)};
+      const unsigned B[3] = {hi_tile(s), lo_tile(s), hi_tile(s)};
+#pragma unroll
+      for (int ks = 0; ks < kXChunk / 8; ++ks)
+#pragma unroll
+        for (int pr = 0; pr < 3; ++pr) {
+          const unsigned accumulate = (i > 0 || ks > 0 || pr > 0) ? 1u : 0u;
+          const unsigned ko = (unsigned)ks * 256;  // two core matrices of 4 configurations
+          mma_tf32(dbase, umma_desc(A[pr] + ko, 128, 512), umma_desc(B[pr] + ko, 128, 512), id1,
+                   accumulate);
+          if (N2 > 0)
+            mma_tf32(dbase + (unsigned)N1,
+                     umma_desc(A[pr] + (unsigned)((R2p - 128) / 8) * 512 + ko, 128, 512),
+                     umma_desc(B[pr] + 16u * 512 + ko, 128, 512), id2, accumulate);
+        }
+      mma_commit(empty(s));
+      if (last_in_group) mma_commit(ready(g & 1));
+      // refill the stage of the previous chunk once its MMAs are done
+      const int nxt = kc - 1 + kGramStages;
+      if (kc >= 1 && nxt < nk) {
+        const int sp = (kc - 1) % kGramStages;
+        if (mbar_wait(empty(sp), (unsigned)((kc - 1) / kGramStages) & 1u)) {
+          bulk_load(hi_tile(sp), src + (size_t)nxt * R2p * kXChunk, copy_bytes, full(sp));
+          ++issued;
+        } else {
+          failed = 1;
+        }
+      }
+    }
+    // the previous group's buffer drains while the tensor core works on this one
+    if (last_in_group && g >= 1) drain(g - 1);
+  }
+  const bool completed = consumed == nk;
+  if (__syncthreads_or(failed) == 0 && completed) drain(n_groups - 1);
+  const int bad = __syncthreads_or(failed || !completed);
+  double sum = 0.0;
+  if (!bad) {
+    const double* Wf = W + (size_t)row_field[r] * n_c * n_c * 2;
+    const int a = (int)tid;  // accumulator row (TMEM lane) of this thread
+    if (a < R2) {
+      for (int j = 0; j < N1 && j < R2; ++j)
+        sum += (j >= 128 ? 2.0 : 1.0) * what(Wf, n_c, a, j) * (double)acc[j * kGramTcThreads + a];
+    }
+    const int a2 = R2p - 128 + a;
+    if (a2 >= 128 && a2 < R2) {
+      for (int jj = 0; jj < N2 && 128 + jj < R2; ++jj)
+        sum += what(Wf, n_c, a2, 128 + jj) * (double)acc[(N1 + jj) * kGramTcThreads + a];
+    }
+  } else {
+    if (tid == 0) {
+      if (err) atomicOr(err, 1);
+      // copies issued but not consumed still land in shared memory; MMAs issued
+      // still run: wait for both before the tensor memory is freed
+      for (int c = consumed; c < issued; ++c)
+        mbar_wait(full(c % kGramStages), (unsigned)(c / kGramStages) & 1u);
+      const unsigned fin = smem_u32(&bars[2 * kGramStages + 2]);
+      mma_commit(fin);  // arrives once every MMA issued so far has completed
+      mbar_wait(fin, 0);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kGramTmemCols)
+                 : "memory");
+  if (!bad) {
+    const double tot = block_sum<kGramTcThreads>(sum, red);
+    if (tid == 0) atomicAdd(integral + r, tot);
+  }
 }
 
 // survival[r] += |psi|^2 over a slice for the flagged rows; psi of a row whose
@@ -978,6 +1556,9 @@ __global__ void __launch_bounds__(256) k_init_state(const SysTab<T> S,
   store4(psi + (size_t)r * S.Zslot * 8 + (size_t)m * 8, v);
 }
 
+// Advances the device-side macro-step counter read by graph-replayed kernels.
+__global__ void k_tick(int* macro_dev) { *macro_dev += 1; }
+
 __global__ void k_zero(double* p, size_t n) {
   const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) p[i] = 0.0;
@@ -1010,12 +1591,43 @@ cudaError_t launch_init_state(const SysTab<T>& S, const double* amps, const long
   return cudaGetLastError();
 }
 
+// The FP32 bulk kernel is only launched from launch_step<float>; the cast
+// lets launch_step<double> compile the (never taken) branch.
 template <typename T>
-cudaError_t launch_step(const SysTab<T>& S, const HamDev<T>* one, int aniso,
+SysTab<float> S_as_float(const SysTab<T>& S) {
+  return *reinterpret_cast<const SysTab<float>*>(&S);
+}
+
+template <typename T>
+cudaError_t launch_step(const SysTab<T>& S, const HamDev<T>* one, int aniso, int bulk,
                         const FieldDev<T>* fields, const int* row_field, const int2* row_win,
-                        int macro, int rows, const T* cur, const T* prev, T* next, T* acc, T* X,
-                        const T* coef, int n_c, int n, int mode, cudaStream_t st) {
+                        int macro, const int* macro_dev, int rows, const T* cur, const T* prev,
+                        T* next, T* acc, T* X, const T* coef, int n_c, int n, int mode,
+                        int xblk, cudaStream_t st) {
   if (rows == 0) return cudaSuccess;
+  if (bulk && sizeof(T) == 4 && one && one->n_half >= kInnerBits && S.Zslot == one->Z &&
+      one->Z % kBulkTile == 0) {
+    const HamDev<float>& hf = *reinterpret_cast<const HamDev<float>*>(one);
+    const size_t smem = (size_t)(1 + bulk_max_partner_tiles(hf)) * kBulkTileBytes;
+    if (smem <= (size_t)kBulkMaxSmem) {
+      static bool attr_set[2] = {false, false};
+      auto kf = aniso ? k_cheb_step_bulk<true> : k_cheb_step_bulk<false>;
+      if (!attr_set[aniso ? 1 : 0]) {
+        cudaError_t e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             kBulkMaxSmem);
+        if (e != cudaSuccess) return e;
+        attr_set[aniso ? 1 : 0] = true;
+      }
+      dim3 grid((unsigned)(one->Z / kBulkTile), rows);
+      kf<<<grid, kBulkTile, smem, st>>>(
+          S_as_float(S), hf, reinterpret_cast<const FieldDev<float>*>(fields), row_field, row_win,
+          macro, macro_dev, reinterpret_cast<const float*>(cur),
+          reinterpret_cast<const float*>(prev), reinterpret_cast<float*>(next),
+          reinterpret_cast<float*>(acc), reinterpret_cast<float*>(X),
+          reinterpret_cast<const float*>(coef), n_c, n, mode, xblk);
+      return cudaGetLastError();
+    }
+  }
   // power-of-two blocks so that m XOR 2^p stays inside the block for 2^p < b
   int b = 32;
   while (b < kStepThreads && b < S.Zslot) b *= 2;
@@ -1027,17 +1639,21 @@ cudaError_t launch_step(const SysTab<T>& S, const HamDev<T>* one, int aniso,
   if (one) {
     if (aniso)
       k_cheb_step<T, true, false><<<grid, b, smem, st>>>(S, h1, fields, row_field, row_win, macro,
-                                                         cur, prev, next, acc, X, coef, n_c, n, mode);
+                                                         macro_dev, cur, prev, next, acc, X, coef,
+                                                         n_c, n, mode, xblk);
     else
       k_cheb_step<T, false, false><<<grid, b, smem, st>>>(S, h1, fields, row_field, row_win, macro,
-                                                          cur, prev, next, acc, X, coef, n_c, n, mode);
+                                                          macro_dev, cur, prev, next, acc, X, coef,
+                                                          n_c, n, mode, xblk);
   } else {
     if (aniso)
       k_cheb_step<T, true, true><<<grid, b, smem, st>>>(S, h1, fields, row_field, row_win, macro,
-                                                        cur, prev, next, acc, X, coef, n_c, n, mode);
+                                                        macro_dev, cur, prev, next, acc, X, coef,
+                                                        n_c, n, mode, xblk);
     else
       k_cheb_step<T, false, true><<<grid, b, smem, st>>>(S, h1, fields, row_field, row_win, macro,
-                                                         cur, prev, next, acc, X, coef, n_c, n, mode);
+                                                         macro_dev, cur, prev, next, acc, X, coef,
+                                                         n_c, n, mode, xblk);
   }
   return cudaGetLastError();
 }
@@ -1050,8 +1666,8 @@ int small_max_configs() {
 template <typename T>
 cudaError_t launch_macro_small(const SysTab<T>& S, const HamDev<T>* one, int aniso,
                                const FieldDev<T>* fields, const int* row_field,
-                               const int2* row_win, int macro, int rows, const T* P, T* Q, T* X,
-                               const T* coef, int n_c, cudaStream_t st) {
+                               const int2* row_win, int macro, const int* macro_dev, int rows,
+                               const T* P, T* Q, T* X, const T* coef, int n_c, cudaStream_t st) {
   if (rows == 0) return cudaSuccess;
   if (S.Zslot > SmallCfg<T>::kMax) return cudaErrorInvalidValue;
   const size_t smem = (size_t)3 * 4 * S.Zslot * sizeof(Cx<T>);
@@ -1067,8 +1683,8 @@ cudaError_t launch_macro_small(const SysTab<T>& S, const HamDev<T>* one, int ani
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
       if (e != cudaSuccess) return e;                                                            \
     }                                                                                              \
-    k_macro_small<T, AN, MU><<<rows, b, smem, st>>>(S, h1, fields, row_field, row_win, macro, P,  \
-                                                    Q, X, coef, n_c);                              \
+    k_macro_small<T, AN, MU><<<rows, b, smem, st>>>(S, h1, fields, row_field, row_win, macro,     \
+                                                    macro_dev, P, Q, X, coef, n_c);                \
   }
   if (one) {
     if (aniso) RP_LAUNCH_SMALL(true, false) else RP_LAUNCH_SMALL(false, false)
@@ -1081,8 +1697,9 @@ cudaError_t launch_macro_small(const SysTab<T>& S, const HamDev<T>* one, int ani
 
 template <typename T>
 cudaError_t launch_gram_integrate(const SysTab<T>& S, const T* X, const double* W,
-                                  const int* row_field, const int2* row_win, int macro, int rows,
-                                  int n_c, double* integral, cudaStream_t st) {
+                                  const int* row_field, const int2* row_win, int macro,
+                                  const int* macro_dev, int rows, int n_c, double* integral,
+                                  cudaStream_t st) {
   if (rows == 0) return cudaSuccess;
   const int nt = n_c / 4;
   const int tiles = nt * (nt + 1) / 2;
@@ -1099,8 +1716,9 @@ cudaError_t launch_gram_integrate(const SysTab<T>& S, const T* X, const double* 
     if (e != cudaSuccess) return e;
   }
   dim3 grid((unsigned)((S.Zslot + z_per_cta - 1) / z_per_cta), rows);
-  k_gram_integrate<T><<<grid, kGramThreads, smem, st>>>(S, X, W, row_field, row_win, macro, n_c,
-                                                        tiles, groups, zc, z_per_cta, integral);
+  k_gram_integrate<T><<<grid, kGramThreads, smem, st>>>(S, X, W, row_field, row_win, macro,
+                                                        macro_dev, n_c, tiles, groups, zc,
+                                                        z_per_cta, integral);
   return cudaGetLastError();
 }
 
@@ -1129,6 +1747,59 @@ cudaError_t launch_stats(const double* per_sample, const long long* off, const l
   return cudaGetLastError();
 }
 
+size_t xblk_floats_per_row(long long Zs, int n_c) { return xblk_row_floats(Zs, n_c); }
+
+size_t gram_tc_smem_bytes(int n_c) {
+  const int R2p = xrows_pad(n_c);
+  const int NT = R2p > 128 ? 2 * R2p - 128 : R2p;
+  const size_t b = (size_t)2 * kGramStages * (R2p > 128 ? R2p : 128) * kXChunk * 4 +
+                   (size_t)NT * kGramTcThreads * 4;
+  return b > (size_t)kGramMinSmem ? b : (size_t)kGramMinSmem;
+}
+
+size_t smem_max_gram_tc() { return gram_tc_smem_bytes(96); }
+
+// both accumulator blocks (2 R2p - 128 columns) fit one 256-column buffer
+bool gram_tc_supported(int n_c) { return n_c >= 8 && n_c <= 96; }
+
+cudaError_t launch_gram_tc(const float* X, const double* W, const int* row_field,
+                           const int2* row_win, int macro, const int* macro_dev, int rows, int n_c,
+                           long long Zs, int n_sm, double* integral, int* err, cudaStream_t st) {
+  if (rows == 0) return cudaSuccess;
+  if (!gram_tc_supported(n_c)) return cudaErrorInvalidValue;
+  const size_t smem = gram_tc_smem_bytes(n_c);
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem_max_gram_tc());
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  // chunks per CTA: the split of each row that minimises (waves of resident
+  // CTAs) x (chunks per CTA + a fixed cost for fill and epilogue)
+  const long long n_chunks = (Zs + kXChunk - 1) / kXChunk;
+  const long long resident = n_sm > 0 ? n_sm : 1;  // one CTA per SM (shared memory)
+  long long per = n_chunks, best = -1;
+  for (long long cpr = 1; cpr <= 256 && cpr <= n_chunks; ++cpr) {
+    const long long p = (n_chunks + cpr - 1) / cpr;
+    const long long ctas = (long long)rows * ((n_chunks + p - 1) / p);
+    const long long cost = ((ctas + resident - 1) / resident) * (p + 24);
+    if (best < 0 || cost < best) {
+      best = cost;
+      per = p;
+    }
+  }
+  dim3 grid((unsigned)((n_chunks + per - 1) / per), rows);
+  k_gram_tc<<<grid, kGramTcThreads, smem, st>>>(X, W, row_field, row_win, macro, macro_dev, n_c, Zs,
+                                                (int)per, integral, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tick(int* macro_dev, cudaStream_t st) {
+  k_tick<<<1, 1, 0, st>>>(macro_dev);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_zero(double* p, size_t n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   k_zero<<<grid1((long long)n, 256), 256, 0, st>>>(p, n);
@@ -1140,18 +1811,18 @@ template cudaError_t launch_coherent_amps<float>(const SysTab<float>&, const lon
 template cudaError_t launch_init_state<float>(const SysTab<float>&, const double*, const long long*,
                                               const int*, const int2*, int, int, float*, float*, double*,
                                               double*, cudaStream_t);
-template cudaError_t launch_step<float>(const SysTab<float>&, const HamDev<float>*, int,
-                                        const FieldDev<float>*, const int*, const int2*, int, int,
-                                        const float*, const float*, float*, float*, float*, const float*, int,
-                                        int, int, cudaStream_t);
+template cudaError_t launch_step<float>(const SysTab<float>&, const HamDev<float>*, int, int,
+                                        const FieldDev<float>*, const int*, const int2*, int,
+                                        const int*, int, const float*, const float*, float*, float*, float*,
+                                        const float*, int, int, int, int, cudaStream_t);
 template cudaError_t launch_gram_integrate<float>(const SysTab<float>&, const float*, const double*,
-                                                  const int*, const int2*, int, int, int, double*,
-                                                  cudaStream_t);
+                                                  const int*, const int2*, int, const int*, int,
+                                                  int, double*, cudaStream_t);
 template int small_max_configs<float>();
 template cudaError_t launch_macro_small<float>(const SysTab<float>&, const HamDev<float>*, int,
                                                const FieldDev<float>*, const int*, const int2*, int,
-                                               int, const float*, float*, float*, const float*, int,
-                                               cudaStream_t);
+                                               const int*, int, const float*, float*, float*,
+                                               const float*, int, cudaStream_t);
 template cudaError_t launch_norm<float>(const SysTab<float>&, const float*, const float*, const int2*,
                                         const int*, int, double*, cudaStream_t);
 template cudaError_t launch_finalize<float>(const SysTab<float>&, const RowsDev&, int, double*,
@@ -1161,18 +1832,18 @@ template cudaError_t launch_coherent_amps<double>(const SysTab<double>&, const l
 template cudaError_t launch_init_state<double>(const SysTab<double>&, const double*, const long long*,
                                               const int*, const int2*, int, int, double*, double*, double*,
                                               double*, cudaStream_t);
-template cudaError_t launch_step<double>(const SysTab<double>&, const HamDev<double>*, int,
-                                        const FieldDev<double>*, const int*, const int2*, int, int,
-                                        const double*, const double*, double*, double*, double*, const double*, int,
-                                        int, int, cudaStream_t);
+template cudaError_t launch_step<double>(const SysTab<double>&, const HamDev<double>*, int, int,
+                                        const FieldDev<double>*, const int*, const int2*, int,
+                                        const int*, int, const double*, const double*, double*, double*, double*,
+                                        const double*, int, int, int, int, cudaStream_t);
 template cudaError_t launch_gram_integrate<double>(const SysTab<double>&, const double*, const double*,
-                                                  const int*, const int2*, int, int, int, double*,
-                                                  cudaStream_t);
+                                                  const int*, const int2*, int, const int*, int,
+                                                  int, double*, cudaStream_t);
 template int small_max_configs<double>();
 template cudaError_t launch_macro_small<double>(const SysTab<double>&, const HamDev<double>*, int,
                                                const FieldDev<double>*, const int*, const int2*, int,
-                                               int, const double*, double*, double*, const double*, int,
-                                               cudaStream_t);
+                                               const int*, int, const double*, double*, double*,
+                                               const double*, int, cudaStream_t);
 template cudaError_t launch_norm<double>(const SysTab<double>&, const double*, const double*, const int2*,
                                         const int*, int, double*, cudaStream_t);
 template cudaError_t launch_finalize<double>(const SysTab<double>&, const RowsDev&, int, double*,

@@ -37,6 +37,16 @@ struct FieldDev {
 
 enum StepMode { MODE_APPLY = 0, MODE_FIRST = 1, MODE_MID = 2, MODE_LAST = 3 };
 
+// Vector passes (multiples of one state vector of every active row) of the
+// Chebyshev term n of a macro-step in the per-term kernels: reads of
+// phi_{n-1} (and phi_{n-2}), write of phi_n (not at the last term), the
+// accumulator write (first term) or read-modify-write, the singlet slices (a
+// quarter each).
+inline double term_vector_passes(int n, int n_c) {
+  if (n == 1) return 3.5;
+  return n == n_c - 1 ? 4.25 : 5.25;
+}
+
 // Per-row (one propagation) metadata, device arrays of length rows.  A row is
 // active in the macro-steps start <= k < end of its window; rows are refilled
 // with new work items as their windows end.
@@ -72,6 +82,7 @@ struct SysTab {
   long long Zslot;
   uint32_t pair_base;
   const uint32_t* pair_of;
+  int* err = nullptr;  // device error word (bit 0: a bounded wait gave up), may be NULL
 };
 
 // ---- launchers (return cudaGetLastError after the launch) ----
@@ -91,12 +102,20 @@ cudaError_t launch_init_state(const SysTab<T>& S, const double* amps, const long
 // One Chebyshev term over every row (see k_cheb_step).  one != NULL: every
 // row is that system (its constants travel as kernel parameters); NULL: each
 // row reads its system from S.ham.  aniso selects the anisotropic hyperfine
-// path (needed if any system of the launch has it).
+// path (needed if any system of the launch has it).  bulk != 0 allows the FP32
+// variant that stages each block's partner tiles with bulk async copies
+// (taken for one system with >= 8 spin-1/2 nuclei whose tiles fit in shared
+// memory; see k_cheb_step_bulk); its bounded wait reports to S.err.
+// macro_dev != NULL: the kernels read the macro-step index from device memory
+// (graph replay; see launch_tick), else they use macro.  xblk != 0 writes the
+// singlet slices in the tensor-core Gram layout (see launch_gram_tc), else as
+// X[row][n][m] complex.
 template <typename T>
-cudaError_t launch_step(const SysTab<T>& S, const HamDev<T>* one, int aniso,
+cudaError_t launch_step(const SysTab<T>& S, const HamDev<T>* one, int aniso, int bulk,
                         const FieldDev<T>* fields, const int* row_field, const int2* row_win,
-                        int macro, int rows, const T* cur, const T* prev, T* next, T* acc, T* X,
-                        const T* coef, int n_c, int n, int mode, cudaStream_t st);
+                        int macro, const int* macro_dev, int rows, const T* cur, const T* prev,
+                        T* next, T* acc, T* X, const T* coef, int n_c, int n, int mode,
+                        int xblk, cudaStream_t st);
 
 // Largest Z (configurations) that launch_macro_small can hold.
 template <typename T>
@@ -109,15 +128,34 @@ int small_max_configs();
 template <typename T>
 cudaError_t launch_macro_small(const SysTab<T>& S, const HamDev<T>* one, int aniso,
                                const FieldDev<T>* fields, const int* row_field,
-                               const int2* row_win, int macro, int rows, const T* P, T* Q, T* X,
-                               const T* coef, int n_c, cudaStream_t st);
+                               const int2* row_win, int macro, const int* macro_dev, int rows,
+                               const T* P, T* Q, T* X, const T* coef, int n_c, cudaStream_t st);
 
 // integral[r] += sum_nm W_nm <x_n|x_m> for the macro-step just finished
 // (x_n = singlet slices X[r][n], W per field); one FP64 atomic per CTA.
 template <typename T>
 cudaError_t launch_gram_integrate(const SysTab<T>& S, const T* X, const double* W,
-                                  const int* row_field, const int2* row_win, int macro, int rows,
-                                  int n_c, double* integral, cudaStream_t st);
+                                  const int* row_field, const int2* row_win, int macro,
+                                  const int* macro_dev, int rows, int n_c, double* integral,
+                                  cudaStream_t st);
+
+// The same time integral on the tensor cores (FP32 singlet slices written by
+// launch_step with xblk = 1; tcgen05.mma kind::tf32 with a hi/lo split of
+// every value, FP64 contraction with W).  n_sm sizes the grid; err receives
+// bit 0 if a bounded wait gave up.  gram_tc_supported: the accumulator blocks
+// of 2 n_c rows fit one 256-column buffer (n_c <= 96).  gram_tc_smem_bytes:
+// dynamic shared memory of one CTA.
+bool gram_tc_supported(int n_c);
+size_t gram_tc_smem_bytes(int n_c);
+cudaError_t launch_gram_tc(const float* X, const double* W, const int* row_field,
+                           const int2* row_win, int macro, const int* macro_dev, int rows, int n_c,
+                           long long Zs, int n_sm, double* integral, int* err, cudaStream_t st);
+
+// Floats per row of the singlet slices in the tensor-core Gram layout.
+size_t xblk_floats_per_row(long long Zs, int n_c);
+
+// *macro_dev += 1 (one thread): ends a graph-replayed macro-step.
+cudaError_t launch_tick(int* macro_dev, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_norm(const SysTab<T>& S, const T* S0, const T* S1, const int2* row_win,

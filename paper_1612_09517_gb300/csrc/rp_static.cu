@@ -288,15 +288,17 @@ rp_status run_static(const rp::HostSystem& hs, int n_fields, const double* field
       for (int r = 0; r < rows; ++r) act += (k < h_win[r].y) ? 1 : 0;
       for (int n = 1; n < n_c; ++n) {
         const int mode = (n == 1) ? rp::MODE_FIRST : (n == n_c - 1 ? rp::MODE_LAST : rp::MODE_MID);
-        L1(rp::launch_step<T>(SYS, &H, H.aniso, d_fdev, d_field, d_win, (int)k, rows, phi[(n - 1) % 3],
+        L1(rp::launch_step<T>(SYS, &H, H.aniso, 0, d_fdev, d_field, d_win, (int)k, nullptr, rows,
+                              phi[(n - 1) % 3],
                               n >= 2 ? phi[(n - 2) % 3] : nullptr,
                               mode == rp::MODE_LAST ? nullptr : phi[n % 3], Q, X, d_coef, n_c, n,
-                              mode, st),
+                              mode, 0, st),
            "step kernel");
         steps++;
       }
       row_terms += act * n_c;
-      L1(rp::launch_gram_integrate<T>(SYS, X, d_W, d_field, d_win, (int)k, rows, n_c, d_int, st),
+      L1(rp::launch_gram_integrate<T>(SYS, X, d_W, d_field, d_win, (int)k, nullptr, rows, n_c,
+                                      d_int, st),
          "gram-integral kernel");
     }
     L1(rp::launch_norm<T>(SYS, S0, S1, d_win, nullptr, rows, d_surv, st), "norm kernel");

@@ -35,7 +35,8 @@ class rp_options(C.Structure):
     _fields_ = [("precision", C.c_int), ("n_cheb", C.c_int), ("tol", C.c_double),
                 ("max_rows", C.c_int), ("deterministic", C.c_int),
                 ("sample_offset", C.c_longlong), ("pair_id", C.c_uint32),
-                ("profile", C.c_int), ("stream", C.c_void_p), ("kernel", C.c_int)]
+                ("profile", C.c_int), ("stream", C.c_void_p), ("kernel", C.c_int),
+                ("gram", C.c_int), ("graph", C.c_int)]
 
 
 class rp_stats(C.Structure):
@@ -44,7 +45,7 @@ class rp_stats(C.Structure):
                 ("step_bytes", C.c_double), ("step_ms", C.c_double),
                 ("step_launches_timed", C.c_longlong), ("device_ms", C.c_double),
                 ("rows", C.c_int), ("n_cheb", C.c_int), ("h2d_bytes", C.c_longlong),
-                ("d2h_bytes", C.c_longlong)]
+                ("d2h_bytes", C.c_longlong), ("graph_launches", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -69,6 +70,15 @@ class rp_cv_options(C.Structure):
 class rp_cv_plan(C.Structure):
     _fields_ = [("M_train", C.c_int), ("cv_threshold", C.c_int), ("n_mc", C.c_longlong),
                 ("net", rp_cv_options)]
+
+
+class rp_tune_result(C.Structure):
+    _fields_ = [("kernel", C.c_int), ("n_cheb", C.c_int), ("graph", C.c_int),
+                ("rate", C.c_double), ("base_rate", C.c_double), ("candidates", C.c_int),
+                ("from_cache", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
@@ -130,6 +140,8 @@ SIGNATURES = [
                                    C.c_uint64, C.c_double, C.POINTER(rp_options),
                                    C.POINTER(C.c_double), C.POINTER(C.c_double),
                                    C.POINTER(rp_stats)]),
+    ("rp_tune", C.c_int, [C.c_void_p, C.c_double, C.c_int, C.POINTER(rp_options),
+                          C.POINTER(rp_options), C.POINTER(rp_tune_result)]),
 ]
 
 
@@ -256,6 +268,16 @@ def rp_yields_static(h, fields, M, seed, t_max, opt=None, per_sample=False, Z=No
     if per_sample:
         res["per_sample"] = ps[: nf * Mr * 3].reshape(nf, Mr, 3)
     return res
+
+
+def rp_tune(h, B, rows, opt=None):
+    """Measured choice of kernel path, n_cheb and graph replay for `rows`
+    concurrent samples at field B; returns (tuned rp_options, result dict)."""
+    o = opt if opt is not None else rp_default_options()
+    tuned = rp_options()
+    res = rp_tune_result()
+    _check(LIB.rp_tune(h, float(B), int(rows), C.byref(o), C.byref(tuned), C.byref(res)))
+    return tuned, res.as_dict()
 
 
 def rp_apply_h(h, B, precision, n_vec, x_ptr, y_ptr, stream=None):

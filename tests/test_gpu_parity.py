@@ -301,3 +301,125 @@ def test_kernel_paths_agree(prec):
         tol = 1e-12 if prec == "fp64" else 2e-6
         assert np.allclose(a["per_sample"], b["per_sample"], rtol=tol, atol=tol * 1e-2)
         assert b["stats"]["step_launches"] < a["stats"]["step_launches"]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_graph_replay_matches_eager(prec):
+    """Macro-steps replayed from CUDA graphs (kernels reading the macro-step
+    index from the device counter) give the eager launches' results, with row
+    refills between replays; uneven systems in one batch too."""
+    rp = _rp()
+    big = wl.random_isotropic(6, 4, two_I=[1] * 10, seed=44, k_S=1.0, k_T=0.4, J=0.1)  # Z = 1024
+    mid = wl.random_isotropic(4, 3, two_I=[1, 1, 1, 2, 1, 1, 2], seed=45, k_S=2.0, k_T=0.5)
+    fields = [0.0, 2.0, 6.0]
+    for s, kern in ((wl.config1().system, 2), (big, 1), (big, 2), (mid, 1)):
+        sy = rp.System(s)
+        a = sy.yields(fields, 5, 3, 1.0, per_sample=True, precision=prec, kernel=kern, max_rows=4)
+        b = sy.yields(fields, 5, 3, 1.0, per_sample=True, precision=prec, kernel=kern, max_rows=4,
+                      graph=1)
+        # the state vectors are bitwise equal; only the order of the FP64
+        # atomics of the time integral may differ
+        assert np.allclose(a["per_sample"], b["per_sample"], rtol=1e-12, atol=1e-14), kern
+        assert b["stats"]["graph_launches"] > 0 and a["stats"]["graph_launches"] == 0
+        assert b["stats"]["step_launches"] == a["stats"]["step_launches"]
+    systems = [wl.config1().system, mid, big]
+    sys_h = [rp.System(s) for s in systems]
+    fl = [np.array([0.0, 2.0]), np.array([1.0, 5.0]), np.array([3.0])]
+    M, T = [4, 3, 2], [1.0, 0.7, 0.5]
+    ra = rp.rp_yields_batch(sys_h, fl, M, T, 9, rp.rp_default_options(precision=prec, max_rows=3))
+    rb = rp.rp_yields_batch(sys_h, fl, M, T, 9,
+                            rp.rp_default_options(precision=prec, max_rows=3, graph=1))
+    for s in range(3):
+        assert np.allclose(ra["out"][s], rb["out"][s], rtol=1e-12, atol=1e-14), s
+    assert rb["stats"]["graph_launches"] > 0
+
+
+def test_autotuner_choice_and_cache(tmp_path, monkeypatch):
+    """rp_tune times its candidates, returns valid settings whose yields agree
+    with the oracle at the FP64 tolerance, and reuses its cache file."""
+    rp = _rp()
+    s = wl.random_isotropic(3, 2, two_I=[1, 2, 1, 1, 1], k_S=1.0, k_T=2.0, seed=46)
+    sy = rp.System(s)
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("RP_TUNE_CACHE", str(cache))
+    base = rp.rp_default_options(precision="fp64")
+    tuned, res = rp.rp_tune(sy.handle, 3.0, 6, base)
+    assert res["candidates"] == 16 and res["from_cache"] == 0  # Z = 48 fits on chip
+    assert res["kernel"] in (1, 2) and res["n_cheb"] in (32, 48, 64, 88) and res["graph"] in (0, 1)
+    assert res["rate"] > 0 and res["rate"] >= res["base_rate"] > 0
+    assert tuned.max_rows == 6 and tuned.precision == rp.RP_FP64
+    tuned2, res2 = rp.rp_tune(sy.handle, 3.0, 6, base)
+    assert res2["from_cache"] == 1 and res2["candidates"] == 0
+    assert (res2["kernel"], res2["n_cheb"], res2["graph"]) == (res["kernel"], res["n_cheb"], res["graph"])
+    assert cache.read_text().count("\n") == 1
+    got = rp.rp_yields(sy.handle, [3.0], 6, 21, 1.5, tuned, True, Z=sy.Z)
+    psi0 = coherent.sample_states(s, 21, range(6))
+    phS, phT, surv = dense.sample_yields(s, 3.0, 1.5, psi0)
+    _cmp_per_sample(got["per_sample"][0], phS, phT, surv, "fp64")
+
+
+@pytest.mark.parametrize("aniso", [False, True])
+def test_bulk_staged_step_matches_direct_and_oracle(aniso):
+    """The FP32 step kernel that stages partner tiles by bulk async copies
+    (kernel 3 with >= 8 spin-1/2 nuclei: here one outer spin-1/2, a spin-1 and
+    a spin-3/2 nucleus outside the 256-configuration tile) equals the kernel
+    that reads partners directly (kernel 1), and the oracle at the FP32
+    tolerance."""
+    rp = _rp()
+    two_I = [1] * 9 + [2, 3]  # Z = 512 * 3 * 4 = 6144
+    gen = wl.random_anisotropic if aniso else wl.random_isotropic
+    s = gen(6, 5, two_I=two_I, k_S=2.0, k_T=0.5, J=0.2, seed=47)
+    sy = rp.System(s)
+    fields = [0.0, 4.0]
+    a = sy.yields(fields, 3, 8, 0.2, per_sample=True, precision="fp32", kernel=1)
+    b = sy.yields(fields, 3, 8, 0.2, per_sample=True, precision="fp32", kernel=3)
+    assert np.allclose(a["per_sample"], b["per_sample"], rtol=1e-12, atol=1e-14)
+    psi0 = coherent.sample_states(s, 8, [1])
+    ref = chebyshev.propagate_yields(s, fields[1], 0.2, psi0[0])
+    got = b["per_sample"][1, 1]
+    assert abs(got[0] - ref[0]) < TOL["fp32"] * abs(ref[0])
+    assert abs(got[1] - ref[1]) < TOL["fp32"] * max(abs(ref[1]), abs(ref[0]))
+    assert abs(got[2] - ref[2]) < TOL["fp32"]
+
+
+@pytest.mark.parametrize("n_cheb", [32, 64, 84, 88])
+def test_tensor_core_time_integral_matches_cuda_core(n_cheb):
+    """The tcgen05 time integral (3xTF32 split, FP64 contraction; gram=2) equals
+    the CUDA-core Gram (gram=1) at FP32 rounding level, for 2 n_cheb below,
+    at and above 128 rows, with padded rows (n_cheb = 84) and a Z that is not
+    a multiple of the 16-configuration chunk; and the oracle at the FP32
+    tolerance."""
+    rp = _rp()
+    s = wl.random_isotropic(4, 3, two_I=[1, 1, 1, 2, 2, 2, 4], k_S=2.0, k_T=0.5, J=0.1, seed=48)
+    sy = rp.System(s)  # Z = 8 * 27 * 5 = 1080
+    fields = [0.0, 3.0]
+    kw = dict(per_sample=True, precision="fp32", kernel=1, n_cheb=n_cheb, max_rows=5)
+    a = sy.yields(fields, 4, 12, 0.5, gram=1, **kw)["per_sample"]
+    b = sy.yields(fields, 4, 12, 0.5, gram=2, **kw)["per_sample"]
+    # phi_S relative; phi_T = 1 - survival - phi_S on the scale of the yields;
+    # survival does not involve the time integral
+    scale = np.maximum(np.abs(a[..., 0]), np.abs(a[..., 1]))
+    assert np.max(np.abs(a[..., 0] - b[..., 0]) / np.abs(a[..., 0])) < 1e-6
+    assert np.max(np.abs(a[..., 1] - b[..., 1]) / scale) < 1e-6
+    assert np.array_equal(a[..., 2], b[..., 2])
+    psi0 = coherent.sample_states(s, 12, [2])
+    ref = chebyshev.propagate_yields(s, fields[1], 0.5, psi0[0])
+    got = b[1, 2]
+    assert abs(got[0] - ref[0]) < TOL["fp32"] * abs(ref[0])
+    assert abs(got[2] - ref[2]) < TOL["fp32"]
+
+
+def test_tensor_core_time_integral_long_accumulation():
+    """Config 2 with few rows, so each CTA of the tensor-core integral covers
+    many chunks: the result stays at FP32 rounding level of the CUDA-core Gram
+    and of the FP64 path (the tensor core's own accumulation is kept to two
+    chunks between drains into FP32 partial sums)."""
+    rp = _rp()
+    sy = rp.System(wl.config2().system)
+    f = [3.0, 20.0]
+    kw = dict(per_sample=True, max_rows=2)
+    a = sy.yields(f, 2, 0, 0.5, precision="fp32", gram=1, **kw)["per_sample"]
+    b = sy.yields(f, 2, 0, 0.5, precision="fp32", gram=2, **kw)["per_sample"]
+    c = sy.yields(f, 2, 0, 0.5, precision="fp64", **kw)["per_sample"]
+    assert np.max(np.abs(b[..., 0] - a[..., 0]) / np.abs(a[..., 0])) < 1e-6
+    assert np.max(np.abs(b[..., 0] - c[..., 0]) / np.abs(c[..., 0])) < 5e-6
