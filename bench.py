@@ -85,7 +85,7 @@ def _peaks():
 
 def _kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("rp_kernels.cu", "rp_kernels.cuh"):
+    for f in ("rp_kernels.cu", "rp_kernels.cuh", "rp_device.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1612_09517_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -246,6 +246,10 @@ def parse():
                          "and print its measured time")
     ap.add_argument("--cv", action="store_true",
                     help="with --converge: use the learned control variate (rp_yields_cv)")
+    ap.add_argument("--cv-bias", action="store_true",
+                    help="config 5: the 128-field curve to SE <= 1e-3 with the learned control "
+                         "variate, then an independent plain M = 2000 estimate at four fields "
+                         "to check its bias; prints one JSON line")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run one small profiling case (192 rows, two macro-steps) and exit")
     return ap.parse_args()
@@ -349,6 +353,35 @@ def main():
                           "M_used": r["M_used"].tolist(),
                           "sigma": [round(float(x), 5) for x in sig],
                           "PhiS": r["out"][:, 0].tolist()}), flush=True)
+        return
+    if args.cv_bias:
+        w5 = wl.config5()
+        o = rp.rp_default_options(precision=prec, stream=torch.cuda.current_stream().cuda_stream)
+        sy.yields([0.0], 2, 0, 0.05)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = rp.rp_yields_cv(sy.handle, w5.fields, SE_TARGET, M_MIN, 4000, 0, w5.t_max, o,
+                            rp.rp_cv_default_plan())
+        wall_cv = time.perf_counter() - t0
+        # independent plain estimate (seed 1: other directions) at four low fields,
+        # where the spread and the control-variate gain are largest
+        idx = [3, 8, 13, 20]
+        t0 = time.perf_counter()
+        p = rp.rp_yields(sy.handle, w5.fields[idx], 2000, 1, w5.t_max, o)
+        wall_plain = time.perf_counter() - t0
+        est, se = r["out"][idx, 0], r["out"][idx, 1]
+        z = (est - p["out"][:, 0]) / np.sqrt(se ** 2 + p["out"][:, 2] ** 2)
+        print(json.dumps({"mode": "cv-bias", "workload": "config5: " + WORKLOAD.split(": ", 1)[1]
+                          .replace("64 fields", "128 fields"),
+                          "wall_cv_s": wall_cv, "max_SE": float(r["out"][:, 1].max()),
+                          "M_plain": r["M_plain"].tolist(), "M_cv": r["M_cv"].tolist(),
+                          "used_cv": [int(x) for x in r["out"][:, 7]],
+                          "bias_fields_mT": [round(float(b), 4) for b in w5.fields[idx]],
+                          "PhiS_cv": est.tolist(), "SE_cv": se.tolist(),
+                          "PhiS_plain_M2000": p["out"][:, 0].tolist(),
+                          "SE_plain_M2000": p["out"][:, 2].tolist(),
+                          "z": z.tolist(), "chi2": float(np.sum(z ** 2)), "dof": len(idx),
+                          "wall_plain_s": wall_plain}), flush=True)
         return
     if args.ncu_case:
         # config-2 system, 3 fields x 64 samples = 192 rows (127 MB per state
