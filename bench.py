@@ -250,6 +250,9 @@ def parse():
                     help="config 5: the 128-field curve to SE <= 1e-3 with the learned control "
                          "variate, then an independent plain M = 2000 estimate at four fields "
                          "to check its bias; prints one JSON line")
+    ap.add_argument("--ncu-case3", action="store_true",
+                    help="profiling case of the anisotropic config-3 system (Z = 2359296): "
+                         "2 rows, two macro-steps, ~4 GB on the device")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run one small profiling case (192 rows, two macro-steps) and exit")
     return ap.parse_args()
@@ -382,6 +385,14 @@ def main():
                           "SE_plain_M2000": p["out"][:, 2].tolist(),
                           "z": z.tolist(), "chi2": float(np.sum(z ** 2)), "dof": len(idx),
                           "wall_plain_s": wall_plain}), flush=True)
+        return
+    if args.ncu_case3:
+        w3 = wl.config3()
+        s3 = rp.System(w3.system)
+        o = rp.rp_default_options(precision=rp.RP_FP32, stream=torch.cuda.current_stream().cuda_stream)
+        h = s3.plan(10.0, w3.t_max, precision=rp.RP_FP32)["h"]
+        rp.rp_yields(s3.handle, np.array([10.0]), 2, 0, 2 * h, o)
+        torch.cuda.synchronize()
         return
     if args.ncu_case:
         # config-2 system, 3 fields x 64 samples = 192 rows (127 MB per state

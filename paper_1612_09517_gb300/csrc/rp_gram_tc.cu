@@ -44,9 +44,10 @@ namespace {
 // holds only the lower-right block) and the CTA adds one FP64 atomic.  Every
 // wait is bounded; a wait that gives up sets bit 0 of the error word, lets
 // the copies and MMAs in flight land, frees tensor memory and returns.
-constexpr int kGramStages = 6;
+constexpr int kGramStages = 6;  // a multiple of kGramGroup
 constexpr int kGramCpgMax = 56;  // partial-sum columns per thread (n_c <= 88)
 constexpr int kGramGroup = 2;  // chunks accumulated in tensor memory before a drain
+static_assert(kGramStages % kGramGroup == 0, "stages hold whole groups");
 constexpr int kGramTcThreads = 512;  // 16 warps: 4 per tensor-memory lane quarter
 constexpr int kGramTmemCols = 512;  // two accumulator buffers, 256 columns apart
 constexpr int kGramMinSmem = 116 * 1024;  // keeps one CTA (and 512 TMEM columns) per SM
@@ -257,12 +258,15 @@ __global__ void __launch_bounds__(kGramTcThreads, 1) k_gram_tc(
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   };
   const int n_groups = (nk + kGramGroup - 1) / kGramGroup;
-  for (int kc = 0; kc < nk; ++kc) {
-    const int s = kc % kGramStages;
-    const int g = kc / kGramGroup, i = kc % kGramGroup;
-    const bool last_in_group = (i == kGramGroup - 1) || (kc == nk - 1);
-    const bool ok = mbar_wait(full(s), (unsigned)(kc / kGramStages) & 1u);
-    if (ok) {
+  // one block barrier per group of kGramGroup chunks (kGramStages is a multiple)
+  for (int g = 0; g < n_groups; ++g) {
+    const int k0 = g * kGramGroup, k1 = min(nk, k0 + kGramGroup);
+    for (int kc = k0; kc < k1; ++kc) {
+      const int s = kc % kGramStages;
+      if (!mbar_wait(full(s), (unsigned)(kc / kGramStages) & 1u)) {
+        failed = 1;
+        continue;
+      }
       float4* h = reinterpret_cast<float4*>(gram_smem + (size_t)(2 * s) * tile_bytes);
       float4* l = reinterpret_cast<float4*>(gram_smem + (size_t)(2 * s + 1) * tile_bytes);
       for (int q = (int)tid; q < R2p * kXChunk / 4; q += kGramTcThreads) {
@@ -273,46 +277,49 @@ __global__ void __launch_bounds__(kGramTcThreads, 1) k_gram_tc(
         l[q] = make_float4(tf32_round(v.x - hv.x), tf32_round(v.y - hv.y), tf32_round(v.z - hv.z),
                            tf32_round(v.w - hv.w));
       }
-    } else {
-      failed = 1;
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (__syncthreads_or(failed)) break;
-    consumed = kc + 1;
+    consumed = k1;
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const unsigned dbase = tmem + (unsigned)(g & 1) * 256u;
-      const unsigned A[3] = {hi_tile(s), hi_tile(s), lo_tile(s)};
-      const unsigned B[3] = {hi_tile(s), lo_tile(s), hi_tile(s)};
+      for (int kc = k0; kc < k1; ++kc) {
+        const int s = kc % kGramStages;
+        const unsigned A[3] = {hi_tile(s), hi_tile(s), lo_tile(s)};
+        const unsigned B[3] = {hi_tile(s), lo_tile(s), hi_tile(s)};
 #pragma unroll
-      for (int ks = 0; ks < kXChunk / 8; ++ks)
+        for (int ks = 0; ks < kXChunk / 8; ++ks)
 #pragma unroll
-        for (int pr = 0; pr < 3; ++pr) {
-          const unsigned accumulate = (i > 0 || ks > 0 || pr > 0) ? 1u : 0u;
-          const unsigned ko = (unsigned)ks * 256;  // two core matrices of 4 configurations
-          mma_tf32(dbase, umma_desc(A[pr] + ko, 128, 512), umma_desc(B[pr] + ko, 128, 512), id1,
-                   accumulate);
-          if (N2 > 0)
-            mma_tf32(dbase + (unsigned)N1,
-                     umma_desc(A[pr] + (unsigned)((R2p - 128) / 8) * 512 + ko, 128, 512),
-                     umma_desc(B[pr] + 16u * 512 + ko, 128, 512), id2, accumulate);
-        }
-      mma_commit(empty(s));
-      if (last_in_group) mma_commit(ready(g & 1));
-      // refill the stage of the previous chunk once its MMAs are done
-      const int nxt = kc - 1 + kGramStages;
-      if (kc >= 1 && nxt < nk) {
-        const int sp = (kc - 1) % kGramStages;
-        if (mbar_wait(empty(sp), (unsigned)((kc - 1) / kGramStages) & 1u)) {
+          for (int pr = 0; pr < 3; ++pr) {
+            const unsigned accumulate = (kc > k0 || ks > 0 || pr > 0) ? 1u : 0u;
+            const unsigned ko = (unsigned)ks * 256;  // two core matrices of 4 configurations
+            mma_tf32(dbase, umma_desc(A[pr] + ko, 128, 512), umma_desc(B[pr] + ko, 128, 512),
+                     id1, accumulate);
+            if (N2 > 0)
+              mma_tf32(dbase + (unsigned)N1,
+                       umma_desc(A[pr] + (unsigned)((R2p - 128) / 8) * 512 + ko, 128, 512),
+                       umma_desc(B[pr] + 16u * 512 + ko, 128, 512), id2, accumulate);
+          }
+        mma_commit(empty(s));
+      }
+      mma_commit(ready(g & 1));
+      // refill the stages of the previous group once its MMAs are done
+      for (int kp = k0 - kGramGroup; kp >= 0 && kp < k0; ++kp) {
+        const int nxt = kp + kGramStages;
+        if (nxt >= nk) break;
+        const int sp = kp % kGramStages;
+        if (mbar_wait(empty(sp), (unsigned)(kp / kGramStages) & 1u)) {
           bulk_load(hi_tile(sp), src + (size_t)nxt * R2p * kXChunk, copy_bytes, full(sp));
           ++issued;
         } else {
           failed = 1;
+          break;
         }
       }
     }
     // the previous group's buffer drains while the tensor core works on this one
-    if (last_in_group && g >= 1) drain(g - 1);
+    if (g >= 1) drain(g - 1);
   }
   const bool completed = consumed == nk;
   if (__syncthreads_or(failed) == 0 && completed) drain(n_groups - 1);
