@@ -71,7 +71,7 @@ typedef struct rp_options {
                              state vectors; time integrals, Chebyshev
                              coefficients and averages are FP64 always */
   int n_cheb;             /* Chebyshev terms per macro-step, multiple of 4 in [8, 88]
-                             (0: 64 FP64, 88 FP32) */
+                             (0: 88) */
   double tol;             /* truncation bound per macro-step (0: 1e-15 FP64, 1e-9 FP32) */
   int max_rows;           /* concurrent propagations (0: from free device memory) */
   int deterministic;      /* 1: trace over the Z basis states |S, M> (Eq. 14)
@@ -91,7 +91,7 @@ typedef struct rp_options {
   int gram;               /* time integral (Eqs. 20, 22) of each macro-step: 0 choose
                              (2 where it applies); 1 CUDA cores (any precision);
                              2 tensor cores (FP32 single systems with the
-                             per-term kernels and n_cheb <= 96: tcgen05.mma
+                             per-term kernels: tcgen05.mma
                              kind::tf32 on hi/lo-split values, FP32 partial
                              sums, FP64 contraction; otherwise falls back to 1) */
   int graph;              /* 1: capture each macro-step's launches (Chebyshev terms

@@ -155,7 +155,7 @@ rp_status run_static(const rp::HostSystem& hs, int n_fields, const double* field
                      uint64_t seed, double t_max, const rp_options& o, double* out,
                      double* per_sample, rp_stats* stats, unsigned char* scratch) {
   cudaStream_t st = (cudaStream_t)o.stream;
-  const int n_c = o.n_cheb > 0 ? o.n_cheb : (o.precision == RP_FP64 ? 64 : 88);
+  const int n_c = o.n_cheb > 0 ? o.n_cheb : 88;
   const double tol = o.tol > 0 ? o.tol : (o.precision == RP_FP64 ? 1e-15 : 1e-9);
   if (n_c % 4 != 0 || n_c < 8 || n_c > 88)
     return sfail(RP_EINVAL, "n_cheb must be a multiple of 4 in [8, 88]");

@@ -179,7 +179,7 @@ rp_status rp_tune(rp_system* s, double B, int rows, const rp_options* base, rp_o
     const double rate = (double)rows * t_trial / (ms * 1e-3);
     r.candidates++;
     const bool is_base = c.kernel == (o.kernel ? o.kernel : (Z <= small_max ? 2 : 1)) &&
-                         c.n_cheb == (o.n_cheb ? o.n_cheb : (o.precision == RP_FP64 ? 64 : 88)) &&
+                         c.n_cheb == (o.n_cheb ? o.n_cheb : 88) &&
                          c.graph == o.graph;
     if (is_base) base_rate = rate;
     if (rate > best) {

@@ -208,7 +208,7 @@ def rp_layout(h, n_nuc):
 
 def rp_plan_field(h, B, t_max, precision=RP_FP64, n_cheb=0, tol=0.0, with_coef=False):
     p = rp_field_plan()
-    n_c = n_cheb or (64 if precision == RP_FP64 else 88)
+    n_c = n_cheb or 88
     coef = np.zeros(2 * n_c) if with_coef else None
     W = np.zeros(2 * n_c * n_c) if with_coef else None
     _check(LIB.rp_plan_field(h, float(B), float(t_max), precision, n_cheb, float(tol), C.byref(p),
