@@ -20,7 +20,7 @@ every field, Eq. 23) = sum_f M_f x (Chebyshev terms of one sample at field f,
 exact from the plan) / (measured terms per second), where M_f are the
 per-field sample counts rp_yields_converged uses for the measured per-field
 spread (SIGMA_PROFILE).  ``python bench.py --converge`` runs that whole
-converged curve once and prints its measured wall time (293 s on GB300).  ``value``
+converged curve once and prints its measured wall time (142.9 s on GB300).  ``value``
 uses device time of the calls (CUDA events on the call's stream, inputs and
 work buffers resident); ``e2e`` uses the wall time of the same C-ABI calls
 with host buffers (planning, host<->device copies and synchronisation inside).
@@ -458,13 +458,13 @@ def main():
     clocks = clk.summary()
 
     # max over ranks of the timed quantities, sums of work
-    vals = torch.tensor([dev_ms, wall_s, region_ms], dtype=torch.float64, device="cuda")
-    work = torch.tensor([row_terms, launches], dtype=torch.float64, device="cuda")
+    row_terms_all, launches_all = row_terms, launches
     if world > 1:
-        torch.distributed.all_reduce(vals, op=torch.distributed.ReduceOp.MAX)
+        from paper_1612_09517_gb300 import shard
+        dev_ms, wall_s, region_ms = shard.max_over_ranks([dev_ms, wall_s, region_ms]).tolist()
+        work = torch.tensor([row_terms, launches], dtype=torch.float64, device="cuda")
         torch.distributed.all_reduce(work, op=torch.distributed.ReduceOp.SUM)
-    dev_ms, wall_s, region_ms = vals.tolist()
-    row_terms_all = work[0].item()
+        row_terms_all, launches_all = work[0].item(), work[1].item()
 
     m_live, sigma_live = _m_needed(samples)
     sigma_max = max(SIGMA_PROFILE)
@@ -539,7 +539,7 @@ def main():
                        "row_terms_per_s": rate_dev, "timed_region_ms": region_ms},
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": int(h2d / max(args.steps, 1)),
                     "d2h_bytes_per_step": int(d2h / max(args.steps, 1))},
-            "gpu_launches": int(work[1].item()),
+            "gpu_launches": int(launches_all),
             "roofline": roofline,
             "clocks": clocks,
             "fp64_plain": fp64,

@@ -1,0 +1,89 @@
+"""Sharding of the samples over ranks (one process per GPU) and the one
+collective of the path.
+
+The stochastic estimate (Eq. 18) averages independent samples, so ranks take
+disjoint contiguous sample ranges (``sample_offset`` of ``rp_yields``; the
+counter-based sampler gives sample s the same directions on every rank) and
+never exchange data while they propagate.  The per-field results are then
+combined with one FP64 all-reduce of five sums per field:
+
+    sum phi_S, sum phi_S^2, sum phi_T, sum phi_T^2, sum survival,
+
+from which the global mean and standard error (Eq. 23, sample variance with
+M - 1) follow exactly.  Each rank's sums are recovered from its own
+``rp_yields`` output (mean and standard error over its M_r samples), so no
+per-sample data crosses ranks.
+
+Host logic only: argument marshalling around ``torch.distributed``; every
+propagation runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def sample_range(M: int, world: int, rank: int):
+    """(offset, count) of rank's contiguous share of samples 0 .. M-1; the
+    first M % world ranks take one sample more."""
+    if world < 1 or not 0 <= rank < world:
+        raise ValueError("need 0 <= rank < world")
+    if M < 0:
+        raise ValueError("M must be >= 0")
+    base, extra = divmod(int(M), int(world))
+    count = base + (1 if rank < extra else 0)
+    offset = rank * base + min(rank, extra)
+    return offset, count
+
+
+def field_sums(out, M: int):
+    """Per-field sums (n_fields, 5) from an rp_yields output block (n_fields, 5)
+    = (Phi_S, Phi_T, SE_S, SE_T, mean survival) over M >= 2 samples."""
+    out = np.asarray(out, dtype=np.float64).reshape(-1, 5)
+    if M < 2:
+        raise ValueError("each rank needs M >= 2 samples (the standard error needs it)")
+    m_s, m_t, se_s, se_t, surv = out.T
+    # sample variance s^2 = M SE^2, sum x^2 = (M - 1) s^2 + M mean^2
+    q_s = (M - 1) * M * se_s ** 2 + M * m_s ** 2
+    q_t = (M - 1) * M * se_t ** 2 + M * m_t ** 2
+    return np.stack([M * m_s, q_s, M * m_t, q_t, M * surv], axis=1)
+
+
+def combine(sums, M: int):
+    """The rp_yields output block over all M samples from summed field_sums."""
+    sums = np.asarray(sums, dtype=np.float64).reshape(-1, 5)
+    if M < 2:
+        raise ValueError("M must be >= 2")
+    s_s, q_s, s_t, q_t, s_u = sums.T
+    m_s, m_t = s_s / M, s_t / M
+    var_s = np.maximum(q_s - M * m_s ** 2, 0.0) / (M - 1)
+    var_t = np.maximum(q_t - M * m_t ** 2, 0.0) / (M - 1)
+    return np.stack([m_s, m_t, np.sqrt(var_s / M), np.sqrt(var_t / M), s_u / M], axis=1)
+
+
+def allreduce_yields(out, M_local: int, group=None):
+    """Combine per-rank rp_yields outputs over the process group: one FP64
+    all-reduce of (5 n_fields + 1) numbers.  Returns (out_global, M_global).
+    Works with the gloo (CPU tensor) and nccl (CUDA tensor) backends."""
+    import torch
+    import torch.distributed as dist
+
+    s = field_sums(out, M_local)
+    flat = np.concatenate([s.ravel(), [float(M_local)]])
+    dev = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+    t = torch.tensor(flat, dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
+    r = t.cpu().numpy()
+    M = int(round(r[-1]))
+    return combine(r[:-1], M), M
+
+
+def max_over_ranks(values, group=None):
+    """Element-wise maximum of per-rank timings (the slowest rank sets the
+    job's time)."""
+    import torch
+    import torch.distributed as dist
+
+    dev = "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+    t = torch.tensor(np.asarray(values, dtype=np.float64), device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    return t.cpu().numpy()
