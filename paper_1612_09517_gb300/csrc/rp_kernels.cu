@@ -402,7 +402,7 @@ __device__ __forceinline__ void step_body(const HamDev<T>& H, const SysTab<T>& S
                                           int n, int mode, int xblk);
 
 template <typename T, bool ANISO, bool MULTI>
-__global__ void __launch_bounds__(kStepThreads, sizeof(T) == 4 ? 4 : 2) k_cheb_step(
+__global__ void __launch_bounds__(kStepThreads, sizeof(T) == 4 ? (ANISO ? 4 : 6) : 2) k_cheb_step(
     const SysTab<T> S, const HamDev<T> H1, const FieldDev<T>* __restrict__ fields,
     const int* __restrict__ row_field, const int2* __restrict__ row_win, int macro_arg,
     const int* __restrict__ macro_dev, const T* __restrict__ cur, const T* __restrict__ prev,
