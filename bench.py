@@ -250,6 +250,10 @@ def parse():
                     help="config 5: the 128-field curve to SE <= 1e-3 with the learned control "
                          "variate, then an independent plain M = 2000 estimate at four fields "
                          "to check its bias; prints one JSON line")
+    ap.add_argument("--table1", action="store_true",
+                    help="the paper's model problem (Table I couplings, Z = 2^20): Phi_S(B) at 21 "
+                         "fields 0-10 mT with M = 200 (and the first 100 samples), the field of "
+                         "the minimum, per-sample histograms at three fields; one JSON line")
     ap.add_argument("--ncu-case3", action="store_true",
                     help="profiling case of the anisotropic config-3 system (Z = 2359296): "
                          "2 rows, two macro-steps, ~4 GB on the device")
@@ -385,6 +389,36 @@ def main():
                           "SE_plain_M2000": p["out"][:, 2].tolist(),
                           "z": z.tolist(), "chi2": float(np.sum(z ** 2)), "dof": len(idx),
                           "wall_plain_s": wall_plain}), flush=True)
+        return
+    if args.table1:
+        gam = 176.085963023
+        s1 = wl.table1(gam)
+        sy1 = rp.System(s1)
+        T1 = 10.0 / min(s1.k_S, s1.k_T)  # survival e^-10 at the horizon
+        B1 = np.linspace(0.0, 10.0, 21)
+        o = rp.rp_default_options(precision=prec, stream=torch.cuda.current_stream().cuda_stream)
+        t0 = time.perf_counter()
+        r = rp.rp_yields(sy1.handle, B1, 200, 0, T1, o, per_sample=True)
+        wall = time.perf_counter() - t0
+        ps = r["per_sample"][:, :, 0]
+        curve = {}
+        for M in (100, 200):
+            x = ps[:, :M]
+            mean, se = x.mean(1), x.std(1, ddof=1) / np.sqrt(M)
+            curve[M] = {"PhiS": mean.round(6).tolist(), "SE": se.round(6).tolist(),
+                        "B_min_mT": float(B1[int(np.argmin(mean))])}
+        hist = {}
+        for b in (0.0, 3.5, 10.0):
+            j = int(np.argmin(np.abs(B1 - b)))
+            h, edges = np.histogram(ps[j], bins=20, range=(0.0, 1.0))
+            hist[str(b)] = {"counts": h.tolist(), "mean": float(ps[j].mean()),
+                            "sd": float(ps[j].std(ddof=1)), "min": float(ps[j].min()),
+                            "max": float(ps[j].max())}
+        print(json.dumps({"mode": "table1", "Z": int(s1.Z), "t_max_us": T1, "fields_mT": B1.tolist(),
+                          "two_J_over_gamma_mT": 2 * s1.J, "wall_s": wall,
+                          "device_ms": r["stats"]["device_ms"], "row_terms": r["stats"]["row_terms"],
+                          "mean_survival": float(r["out"][:, 4].max()),
+                          "M100": curve[100], "M200": curve[200], "hist": hist}), flush=True)
         return
     if args.ncu_case3:
         w3 = wl.config3()

@@ -267,10 +267,10 @@ class YieldEngine {
     row_sys_ = ar_.get<int>(R);
     small_ = (o_.kernel == 2 || (o_.kernel == 0 && Zslot_ <= rp::small_max_configs<T>())) &&
              Zslot_ <= rp::small_max_configs<T>();
-    // tensor-core time integral: FP32, one system (the slices of every row cover
-    // the same Z, so the zero padding of the last chunk stays zero), per-term kernels
-    tc_gram_ = sizeof(T) == 4 && sys_.size() == 1 && !small_ && o_.gram != 1 &&
-               rp::gram_tc_supported(n_c_);
+    // tensor-core time integral: FP32 with the per-term kernels (each row's
+    // integral covers its own system's Z; the step kernel keeps the padding of
+    // the last 16-configuration chunk at zero)
+    tc_gram_ = sizeof(T) == 4 && !small_ && o_.gram != 1 && rp::gram_tc_supported(n_c_);
     const size_t x_row = std::max<size_t>((size_t)n_c_ * Zslot_ * 2,
                                           rp::xblk_floats_per_row(Zslot_, n_c_));
     X_ = ar_.get<T>((size_t)R * x_row);
@@ -462,7 +462,10 @@ class YieldEngine {
     if (ev_steps) ck(cudaEventRecord(ev_steps, s), "cudaEventRecord");
     if (tc_gram_)
       ck(rp::launch_gram_tc(reinterpret_cast<const float*>(X_), d_W_, rows_.field, rows_.win, k,
-                            mdev, R_, n_c_, Zslot_, n_sm_, rows_.integral, d_err_, s),
+                            mdev, R_, n_c_, Zslot_,
+                            reinterpret_cast<const rp::HamDev<float>*>(d_ham_),
+                            sys_.size() == 1 ? nullptr : row_sys_, n_sm_, rows_.integral, d_err_,
+                            s),
          "tensor-core time-integral kernel");
     else
       ck(rp::launch_gram_integrate<T>(S_, X_, d_W_, rows_.field, rows_.win, k, mdev, R_, n_c_,

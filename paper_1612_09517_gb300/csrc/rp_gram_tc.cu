@@ -163,14 +163,17 @@ __device__ __forceinline__ double what(const double* __restrict__ Wf, int n_c, i
 __global__ void __launch_bounds__(kGramTcThreads, 1) k_gram_tc(
     const float* __restrict__ X, const double* __restrict__ W, const int* __restrict__ row_field,
     const int2* __restrict__ row_win, int macro_arg, const int* __restrict__ macro_dev, int n_c,
-    long long Zs, int chunks_per_cta, double* __restrict__ integral, int* __restrict__ err) {
+    long long Zs, const HamDev<float>* __restrict__ ham, const int* __restrict__ row_sys,
+    int chunks_per_cta, double* __restrict__ integral, int* __restrict__ err) {
   const int r = blockIdx.y;
   {
     const int macro = macro_dev ? *macro_dev : macro_arg;
     const int2 w = row_win[r];
     if (macro < w.x || macro >= w.y) return;
   }
-  const int n_chunks = (int)((Zs + kXChunk - 1) / kXChunk);
+  // chunks of this row's own system (rows of one launch may differ in Z)
+  const long long Zr = ham[row_sys ? row_sys[r] : 0].Z;
+  const int n_chunks = (int)((Zr + kXChunk - 1) / kXChunk);
   const int c_begin = blockIdx.x * chunks_per_cta;
   const int nk = min(n_chunks - c_begin, chunks_per_cta);
   if (nk <= 0) return;
@@ -380,7 +383,8 @@ bool gram_tc_supported(int n_c) { return n_c >= 8 && n_c <= 88; }
 
 cudaError_t launch_gram_tc(const float* X, const double* W, const int* row_field,
                            const int2* row_win, int macro, const int* macro_dev, int rows, int n_c,
-                           long long Zs, int n_sm, double* integral, int* err, cudaStream_t st) {
+                           long long Zs, const HamDev<float>* ham, const int* row_sys, int n_sm,
+                           double* integral, int* err, cudaStream_t st) {
   if (rows == 0) return cudaSuccess;
   if (!gram_tc_supported(n_c)) return cudaErrorInvalidValue;
   const size_t smem = gram_tc_smem_bytes(n_c);
@@ -407,7 +411,7 @@ cudaError_t launch_gram_tc(const float* X, const double* W, const int* row_field
   }
   dim3 grid((unsigned)((n_chunks + per - 1) / per), rows);
   k_gram_tc<<<grid, kGramTcThreads, smem, st>>>(X, W, row_field, row_win, macro, macro_dev, n_c, Zs,
-                                                (int)per, integral, err);
+                                                ham, row_sys, (int)per, integral, err);
   return cudaGetLastError();
 }
 

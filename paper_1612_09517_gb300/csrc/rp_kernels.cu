@@ -458,7 +458,16 @@ __device__ __forceinline__ void step_body(const HamDev<T>& H, const SysTab<T>& S
   }
   tile_put(tile, blockDim.x, threadIdx.x, a);
   __syncthreads();
-  if (!valid) return;  // no barrier below
+  if (!valid) {  // no barrier below
+    // the tensor-core integral reads whole 16-configuration chunks: keep the
+    // padding past Z at zero (a refilled row may hold a larger system's slices)
+    if (xblk && mode != MODE_APPLY && m < ((Z + kXChunk - 1) / kXChunk) * kXChunk) {
+      const Cx<T> zero[4] = {{T(0), T(0)}, {T(0), T(0)}, {T(0), T(0)}, {T(0), T(0)}};
+      store_singlet_blk(xblk_addr(X, r, n, m, S.Zslot, n_c), zero);
+      if (mode == MODE_FIRST) store_singlet_blk(xblk_addr(X, r, 0, m, S.Zslot, n_c), zero);
+    }
+    return;
+  }
 
   Cx<T> y[4];
 #pragma unroll

@@ -141,7 +141,9 @@ cudaError_t launch_gram_integrate(const SysTab<T>& S, const T* X, const double* 
 
 // The same time integral on the tensor cores (FP32 singlet slices written by
 // launch_step with xblk = 1; tcgen05.mma kind::tf32 with a hi/lo split of
-// every value, FP64 contraction with W).  n_sm sizes the grid; err receives
+// every value, FP64 contraction with W).  Row r covers the configurations of
+// its system ham[row_sys[r]] (row_sys NULL: system 0); Zs is the slot stride.
+// n_sm sizes the grid; err receives
 // bit 0 if a bounded wait gave up.  gram_tc_supported: the accumulator blocks
 // of 2 n_c rows fit one 256-column buffer (n_c <= 96).  gram_tc_smem_bytes:
 // dynamic shared memory of one CTA.
@@ -149,7 +151,8 @@ bool gram_tc_supported(int n_c);
 size_t gram_tc_smem_bytes(int n_c);
 cudaError_t launch_gram_tc(const float* X, const double* W, const int* row_field,
                            const int2* row_win, int macro, const int* macro_dev, int rows, int n_c,
-                           long long Zs, int n_sm, double* integral, int* err, cudaStream_t st);
+                           long long Zs, const HamDev<float>* ham, const int* row_sys, int n_sm,
+                           double* integral, int* err, cudaStream_t st);
 
 // Floats per row of the singlet slices in the tensor-core Gram layout.
 size_t xblk_floats_per_row(long long Zs, int n_c);

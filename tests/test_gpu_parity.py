@@ -423,3 +423,26 @@ def test_tensor_core_time_integral_long_accumulation():
     c = sy.yields(f, 2, 0, 0.5, precision="fp64", **kw)["per_sample"]
     assert np.max(np.abs(b[..., 0] - a[..., 0]) / np.abs(a[..., 0])) < 1e-6
     assert np.max(np.abs(b[..., 0] - c[..., 0]) / np.abs(c[..., 0])) < 5e-6
+
+
+def test_tensor_core_time_integral_uneven_batch():
+    """rp_yields_batch with systems of different Z (none a multiple of the
+    16-configuration chunk) sharing rows that are refilled across systems: the
+    tensor-core integral (each row over its own Z, zero padding kept by the
+    step kernel) equals the CUDA-core Gram at FP32 rounding level."""
+    rp = _rp()
+    systems = [wl.random_isotropic(4, 3, two_I=[1, 1, 1, 2, 2, 2, 4], seed=50, k_S=2.0, k_T=0.5),
+               wl.random_isotropic(5, 4, two_I=[1] * 7 + [2, 2], seed=51, k_S=1.0, k_T=1.0),
+               wl.random_anisotropic(4, 4, two_I=[1, 1, 1, 1, 2, 2, 2, 2], seed=52, k_S=0.5,
+                                     k_T=3.0, J=0.2)]
+    assert sorted(s.Z for s in systems) == [1080, 1152, 1296]
+    sys_h = [rp.System(s) for s in systems]
+    fl = [np.array([0.0, 4.0]), np.array([1.0, 6.0]), np.array([2.0])]
+    M, T = [3, 3, 4], [0.4, 0.3, 0.5]
+    kw = dict(precision="fp32", kernel=1, max_rows=3)
+    a = rp.rp_yields_batch(sys_h, fl, M, T, 5, rp.rp_default_options(gram=1, **kw))
+    b = rp.rp_yields_batch(sys_h, fl, M, T, 5, rp.rp_default_options(gram=2, **kw))
+    for s in range(3):
+        A, B = a["out"][s], b["out"][s]
+        assert np.max(np.abs(A[:, 0] - B[:, 0]) / np.abs(A[:, 0])) < 1e-6, s
+        assert np.max(np.abs(A[:, 1] - B[:, 1]) / np.maximum(np.abs(A[:, 1]), np.abs(A[:, 0]))) < 1e-6
