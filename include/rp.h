@@ -378,6 +378,24 @@ rp_status rp_yields_static(rp_system* sys, int n_fields, const double* fields, i
                            uint64_t seed, double t_max, const rp_options* opt, double* out,
                            double* per_sample, rp_stats* stats);
 
+/* Time-resolved observables of one field (Eq. 18 with A = P_S, P_T and the
+ * identity; Eqs. 3-4): the sample means of
+ *   P_S(t) = |<S|psi(t)>|^2,  P_T(t) = |psi(t)|^2 - P_S(t),  survival |psi(t)|^2
+ * at the macro-step boundaries t_i = i h, i = 0 .. n_macro (h from
+ * rp_plan_field), over M coherent-state samples (or the Z basis states of
+ * Eq. 14 when opt->deterministic).  psi(0) = |S> x nuclear state, so the first
+ * point is (1, 0, 1).  The same propagation as rp_yields; graph replay is not
+ * used.
+ *   max_times  capacity of t and out (in time points)
+ *   n_times    [out] n_macro + 1
+ *   t          [n_times] host, us;  out [n_times * 3] host: P_S, P_T, survival
+ * With t or out NULL only *n_times is set (a size query).
+ * Errors: RP_EINVAL (max_times < n_times, M < 1, bad options), RP_ENOTCONV,
+ * RP_ECUDA, RP_ENOMEM, RP_ENODEV. */
+rp_status rp_time_trace(rp_system* sys, double B, int M, uint64_t seed, double t_max,
+                        const rp_options* opt, int max_times, int* n_times, double* t,
+                        double* out);
+
 /* Launch-configuration autotuner (the paper has no counterpart: its method
  * ran serially on CPUs).  For one system, precision and concurrency it times
  * the candidates

@@ -364,7 +364,7 @@ class YieldEngine {
       // profile events bracket the step kernels (eager) or the whole graph replay
       cudaEvent_t ev_end = o_.profile ? pev.back() : nullptr;
       int n_step = 0;
-      if (!o_.graph) {
+      if (!o_.graph || d_trace_) {
         n_step = issue(k, st_, nullptr, ev_end);
         launches += n_step + 1;
       } else if (k < 2) {
@@ -387,6 +387,11 @@ class YieldEngine {
       }
       step_bytes_all += bytes;
       row_terms += act * (long long)n_c_;
+      if (d_trace_) {
+        T* Sb2[2] = {S0_, S1_};
+        launched(rp::launch_trace<T>(S_, Sb2[(k + 1) & 1], rows_.win, k, R_, d_trace_, st_),
+                 "trace kernel");
+      }
       // rows whose window ends after this macro-step: finish and refill
       bool any = false;
       for (int r = 0; r < R; ++r) {
@@ -424,6 +429,9 @@ class YieldEngine {
   }
 
   void set_seed(uint64_t seed) { seed_ = seed; }
+
+  // Time-resolved sums (launch_trace) after every macro-step; eager launches.
+  void set_trace(double* trace) { d_trace_ = trace; }
 
   long long graph_launches = 0;
 
@@ -502,6 +510,7 @@ class YieldEngine {
   }
 
   int* d_err_ = nullptr;
+  double* d_trace_ = nullptr;
   cudaGraphExec_t gexec_[2] = {nullptr, nullptr};
   int gsteps_[2] = {0, 0};
   cudaStream_t cap_st_ = nullptr;
@@ -670,6 +679,53 @@ rp_status run_yields(rp_system* sys, int n_fields, const double* fields, int M, 
     fill_stats(stats, eng, n_items, R, n_c, ev.a, ev.b, o.profile != 0, d2h);
   }
   ck(cudaStreamSynchronize(st), "free");
+  return RP_OK;
+}
+
+// Time-resolved P_S(t), P_T(t) and survival (Eq. 18 with A = P_S, P_T, 1)
+// at the macro-step boundaries t_i = i h of one field, averaged over the
+// samples (or the Z basis states when deterministic).
+template <typename T>
+rp_status run_time_trace(rp_system* sys, double B, int M, uint64_t seed, double t_max,
+                         const rp_options& o, int n_times, double* t, double* out) {
+  const rp::HostSystem& hs = sys->hs;
+  cudaStream_t st = (cudaStream_t)o.stream;
+  const int n_c = o.n_cheb > 0 ? o.n_cheb : default_ncheb(o.precision);
+  const double tol = o.tol > 0 ? o.tol : default_tol(o.precision);
+  const long long Mr = o.deterministic ? hs.Z : (long long)M;
+  std::vector<rp::FieldPlan> plans;
+  rp_status ps = plan_all(hs, 1, &B, t_max, n_c, tol, plans);
+  if (ps != RP_OK) return ps;
+  std::vector<long long> first(1, 0), count(1, Mr), out0(1, 0);
+  const std::vector<Item> items = make_items(plans, first, count, out0, o.sample_offset, o.deterministic);
+  const int R = choose_rows<T>(hs, o, n_c, (long long)items.size());
+  std::vector<double> h_tr(2 * (size_t)n_times, 0.0);
+  {
+    Arena ar(st);
+    YieldEngine<T> eng({&hs}, o, n_c, st, ar);
+    eng.set_seed(seed);
+    eng.set_fields(plans);
+    eng.alloc_rows(R);
+    double* d_ps = ar.get<double>(items.size() * 3);
+    double* d_tr = ar.get<double>(2 * (size_t)n_times);
+    ck(cudaMemsetAsync(d_tr, 0, 2 * (size_t)n_times * sizeof(double), st), "cudaMemsetAsync");
+    eng.set_trace(d_tr);
+    eng.run(items, d_ps);
+    ck(cudaMemcpyAsync(h_tr.data(), d_tr, h_tr.size() * sizeof(double), cudaMemcpyDeviceToHost, st),
+       "d2h trace");
+    ck(cudaStreamSynchronize(st), "kernel execution");
+  }
+  ck(cudaStreamSynchronize(st), "free");
+  const double h = plans[0].h;
+  for (int i = 0; i < n_times; ++i) {
+    t[i] = i * h;
+    // psi(0) = |S> x (normalised nuclear state): P_S = survival = 1, P_T = 0
+    const double p_s = i == 0 ? 1.0 : h_tr[2 * (size_t)i] / (double)Mr;
+    const double surv = i == 0 ? 1.0 : h_tr[2 * (size_t)i + 1] / (double)Mr;
+    out[3 * (size_t)i] = p_s;
+    out[3 * (size_t)i + 1] = surv - p_s;  // P_T = 1 - P_S on the electrons
+    out[3 * (size_t)i + 2] = surv;
+  }
   return RP_OK;
 }
 
@@ -1354,6 +1410,44 @@ rp_status rp_yields(rp_system* s, int n_fields, const double* fields, int M, uin
     if (o.precision == RP_FP64)
       return run_yields<double>(s, n_fields, fields, M, seed, t_max, o, out, per_sample, stats);
     return run_yields<float>(s, n_fields, fields, M, seed, t_max, o, out, per_sample, stats);
+  } catch (const CudaFail& e) {
+    return fail(e.st, e.msg);
+  } catch (const std::bad_alloc&) {
+    return fail(RP_ENOMEM, "host allocation failed");
+  }
+}
+
+rp_status rp_time_trace(rp_system* s, double B, int M, uint64_t seed, double t_max,
+                        const rp_options* opt, int max_times, int* n_times, double* t,
+                        double* out) {
+  g_err.clear();
+  rp_options o;
+  if (opt) o = *opt;
+  else rp_default_options(&o);
+  if (!s || !n_times) return fail(RP_EINVAL, "system or n_times is NULL");
+  if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
+  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..3, gram 0..2 and graph 0 or 1");
+  if (!o.deterministic && M < 1) return fail(RP_EINVAL, "M must be >= 1");
+  if (!(t_max > 0.0) || !std::isfinite(t_max)) return fail(RP_EINVAL, "t_max must be positive and finite");
+  if (!std::isfinite(B)) return fail(RP_EINVAL, "non-finite field");
+  if (o.sample_offset < 0) return fail(RP_EINVAL, "sample_offset must be >= 0");
+  const int n_c = o.n_cheb > 0 ? o.n_cheb : default_ncheb(o.precision);
+  if (n_c % 4 != 0 || n_c < 8 || n_c > 88)
+    return fail(RP_EINVAL, "n_cheb must be a multiple of 4 in [8, 88]");
+  try {
+    std::vector<rp::FieldPlan> plans;
+    rp_status ps = plan_all(s->hs, 1, &B, t_max, n_c, o.tol > 0 ? o.tol : default_tol(o.precision),
+                            plans);
+    if (ps != RP_OK) return ps;
+    if (plans[0].n_macro + 1 > (long long)INT32_MAX) return fail(RP_EINVAL, "too many time points");
+    const int nt = (int)(plans[0].n_macro + 1);
+    *n_times = nt;
+    if (!t || !out) return RP_OK;  // size query
+    if (max_times < nt) return fail(RP_EINVAL, "max_times is smaller than the number of time points");
+    rp_status ds = check_device();
+    if (ds != RP_OK) return ds;
+    if (o.precision == RP_FP64) return run_time_trace<double>(s, B, M, seed, t_max, o, nt, t, out);
+    return run_time_trace<float>(s, B, M, seed, t_max, o, nt, t, out);
   } catch (const CudaFail& e) {
     return fail(e.st, e.msg);
   } catch (const std::bad_alloc&) {

@@ -1043,6 +1043,41 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_integrate(
   if (tid == 0) atomicAdd(integral + r, tot);
 }
 
+// Time-resolved observables (Eq. 18 for A = P_S and A = 1): after macro-step
+// k, every row active in it holds psi(t_i), i = k + 1 - start, in Q; adds
+// |<S|psi>|^2 (P_S = |S><S| on the electrons, identity on the nuclei) and
+// |psi|^2 over a slice of its configurations into trace[2 i] and
+// trace[2 i + 1] (FP64, summed over rows).
+template <typename T>
+__global__ void __launch_bounds__(256) k_trace(const SysTab<T> ST, const T* __restrict__ Q,
+                                               const int2* __restrict__ row_win, int macro,
+                                               long long z_per_cta, double* __restrict__ trace) {
+  __shared__ double sh[256];
+  const int r = blockIdx.y;
+  const int2 w = row_win[r];
+  if (macro < w.x || macro >= w.y) return;
+  const long long Z = ST.ham[ST.row_sys ? ST.row_sys[r] : 0].Z;
+  const T* S = Q + (size_t)r * ST.Zslot * 8;
+  const long long z0 = (long long)blockIdx.x * z_per_cta;
+  const long long z1 = min(Z, z0 + z_per_cta);
+  double ps = 0.0, nn = 0.0;
+  for (long long m = z0 + threadIdx.x; m < z1; m += blockDim.x) {
+    Cx<T> a[4];
+    load4(S + m * 8, a);
+    const double dr = (double)a[1].re - (double)a[2].re, di = (double)a[1].im - (double)a[2].im;
+    ps += 0.5 * (dr * dr + di * di);
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      nn += (double)a[e].re * (double)a[e].re + (double)a[e].im * (double)a[e].im;
+  }
+  const int i = macro + 1 - w.x;
+  const double tps = block_sum<256>(ps, sh);
+  if (threadIdx.x == 0) atomicAdd(trace + 2 * i, tps);
+  __syncthreads();
+  const double tnn = block_sum<256>(nn, sh);
+  if (threadIdx.x == 0) atomicAdd(trace + 2 * i + 1, tnn);
+}
+
 // survival[r] += |psi|^2 over a slice for the flagged rows; psi of a row whose
 // window ended at macro-step e sits in S[e % 2].
 template <typename T>
@@ -1431,6 +1466,16 @@ cudaError_t launch_stats(const double* per_sample, const long long* off, const l
 
 size_t xblk_floats_per_row(long long Zs, int n_c) { return xblk_row_floats(Zs, n_c); }
 
+template <typename T>
+cudaError_t launch_trace(const SysTab<T>& S, const T* Q, const int2* row_win, int macro, int rows,
+                         double* trace, cudaStream_t st) {
+  if (rows == 0) return cudaSuccess;
+  const long long zper = 8192;
+  dim3 grid(grid1(S.Zslot, (int)zper), rows);
+  k_trace<T><<<grid, 256, 0, st>>>(S, Q, row_win, macro, zper, trace);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_tick(int* macro_dev, cudaStream_t st) {
   k_tick<<<1, 1, 0, st>>>(macro_dev);
   return cudaGetLastError();
@@ -1461,6 +1506,8 @@ template cudaError_t launch_macro_small<float>(const SysTab<float>&, const HamDe
                                                const float*, int, cudaStream_t);
 template cudaError_t launch_norm<float>(const SysTab<float>&, const float*, const float*, const int2*,
                                         const int*, int, double*, cudaStream_t);
+template cudaError_t launch_trace<float>(const SysTab<float>&, const float*, const int2*, int, int,
+                                         double*, cudaStream_t);
 template cudaError_t launch_finalize<float>(const SysTab<float>&, const RowsDev&, int, double*,
                                             cudaStream_t);
 template cudaError_t launch_coherent_amps<double>(const SysTab<double>&, const long long*, const int*,
@@ -1482,6 +1529,8 @@ template cudaError_t launch_macro_small<double>(const SysTab<double>&, const Ham
                                                const double*, int, cudaStream_t);
 template cudaError_t launch_norm<double>(const SysTab<double>&, const double*, const double*, const int2*,
                                         const int*, int, double*, cudaStream_t);
+template cudaError_t launch_trace<double>(const SysTab<double>&, const double*, const int2*, int, int,
+                                         double*, cudaStream_t);
 template cudaError_t launch_finalize<double>(const SysTab<double>&, const RowsDev&, int, double*,
                                             cudaStream_t);
 

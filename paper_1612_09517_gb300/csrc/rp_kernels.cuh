@@ -160,6 +160,12 @@ size_t xblk_floats_per_row(long long Zs, int n_c);
 // *macro_dev += 1 (one thread): ends a graph-replayed macro-step.
 cudaError_t launch_tick(int* macro_dev, cudaStream_t st);
 
+// After macro-step `macro`: trace[2 i] += |<S|psi>|^2, trace[2 i + 1] += |psi|^2
+// for every row active in it, psi = psi(t_i) in Q, i = macro + 1 - start.
+template <typename T>
+cudaError_t launch_trace(const SysTab<T>& S, const T* Q, const int2* row_win, int macro, int rows,
+                         double* trace, cudaStream_t st);
+
 template <typename T>
 cudaError_t launch_norm(const SysTab<T>& S, const T* S0, const T* S1, const int2* row_win,
                         const int* row_flag, int rows, double* survival, cudaStream_t st);

@@ -140,6 +140,9 @@ SIGNATURES = [
                                    C.c_uint64, C.c_double, C.POINTER(rp_options),
                                    C.POINTER(C.c_double), C.POINTER(C.c_double),
                                    C.POINTER(rp_stats)]),
+    ("rp_time_trace", C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_uint64, C.c_double,
+                                C.POINTER(rp_options), C.c_int, C.POINTER(C.c_int),
+                                C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     ("rp_tune", C.c_int, [C.c_void_p, C.c_double, C.c_int, C.POINTER(rp_options),
                           C.POINTER(rp_options), C.POINTER(rp_tune_result)]),
 ]
@@ -268,6 +271,20 @@ def rp_yields_static(h, fields, M, seed, t_max, opt=None, per_sample=False, Z=No
     if per_sample:
         res["per_sample"] = ps[: nf * Mr * 3].reshape(nf, Mr, 3)
     return res
+
+
+def rp_time_trace(h, B, M, seed, t_max, opt=None):
+    """Sample means of P_S(t), P_T(t) and survival at the macro-step boundaries:
+    returns (t, out) with out[:, 0] = P_S, out[:, 1] = P_T, out[:, 2] = survival."""
+    o = opt if opt is not None else rp_default_options()
+    n = C.c_int(0)
+    _check(LIB.rp_time_trace(h, float(B), int(M), C.c_uint64(int(seed)), float(t_max), C.byref(o),
+                             0, C.byref(n), None, None))
+    t = np.zeros(n.value)
+    out = np.zeros(3 * n.value)
+    _check(LIB.rp_time_trace(h, float(B), int(M), C.c_uint64(int(seed)), float(t_max), C.byref(o),
+                             n.value, C.byref(n), _dptr(t), _dptr(out)))
+    return t, out.reshape(-1, 3)
 
 
 def rp_tune(h, B, rows, opt=None):

@@ -139,3 +139,22 @@ def test_yields_reports_missing_device_loudly():
     sy = rp.System(wl.config1().system)
     with pytest.raises(rp.RPError, match="RP_ENODEV"):
         sy.yields([0.0], 4, 0, 1.0)
+
+
+def test_time_trace_size_query_and_capacity():
+    """rp_time_trace reports n_macro + 1 time points without a GPU and refuses a
+    too small output buffer before any device work."""
+    s = wl.random_isotropic(2, 1, seed=9)
+    sy = rp.System(s)
+    p = sy.plan(1.5, 2.0)
+    o = rp.rp_default_options(precision=rp.RP_FP64)
+    n = ctypes.c_int(0)
+    assert rp.LIB.rp_time_trace(sy.handle, 1.5, 4, ctypes.c_uint64(0), 2.0, ctypes.byref(o), 0,
+                                ctypes.byref(n), None, None) == 0
+    assert n.value == p["n_macro"] + 1
+    t = np.zeros(n.value)
+    out = np.zeros(3 * n.value)
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    st = rp.LIB.rp_time_trace(sy.handle, 1.5, 4, ctypes.c_uint64(0), 2.0, ctypes.byref(o),
+                              n.value - 1, ctypes.byref(n), dp(t), dp(out))
+    assert st == 1  # RP_EINVAL

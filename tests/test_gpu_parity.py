@@ -446,3 +446,43 @@ def test_tensor_core_time_integral_uneven_batch():
         A, B = a["out"][s], b["out"][s]
         assert np.max(np.abs(A[:, 0] - B[:, 0]) / np.abs(A[:, 0])) < 1e-6, s
         assert np.max(np.abs(A[:, 1] - B[:, 1]) / np.maximum(np.abs(A[:, 1]), np.abs(A[:, 0]))) < 1e-6
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_time_trace_closed_form_one_nucleus(prec):
+    """P_S(t), P_T(t), survival at the macro-step boundaries for one spin-1/2
+    (a = 1 mT, k_S = k_T = 1, B = 0): the trace over the Z = 2 basis states
+    equals e^{-kt} (5/8 + 3/8 cos(a t)) and the survival e^{-kt}."""
+    rp = _rp()
+    s = wl.one_nucleus(1.0, k=1.0)
+    sy = rp.System(s)
+    t, out = rp.rp_time_trace(sy.handle, 0.0, 2, 0, 2.0,
+                              rp.rp_default_options(precision=prec, deterministic=1))
+    a = 176.085963023
+    ps = np.exp(-t) * (5 / 8 + 3 / 8 * np.cos(a * t))
+    tol = TOL[prec]
+    assert abs(t[-1] - 2.0) < 1e-12 and t.size > 3
+    assert np.max(np.abs(out[:, 0] - ps)) < tol
+    assert np.max(np.abs(out[:, 2] - np.exp(-t))) < tol
+    assert np.max(np.abs(out[:, 1] - (np.exp(-t) - ps))) < tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_time_trace_matches_dense_oracle(prec):
+    """Sample means of P_S(t) and survival on the config-1 system (k_S != k_T
+    variant) at B = 2 mT against direct matrix exponentials of the oracle."""
+    rp = _rp()
+    s = wl.random_isotropic(3, 1, two_I=[1, 2, 1, 1], k_S=2.0, k_T=0.5, J=0.2, seed=53)
+    sy = rp.System(s)
+    M, B, T = 5, 2.0, 1.0
+    t, out = rp.rp_time_trace(sy.handle, B, M, 7, T, rp.rp_default_options(precision=prec))
+    psi0 = coherent.sample_states(s, 7, range(M))
+    ps = np.mean([dense.singlet_probability(s, B, p, t) for p in psi0], axis=0)
+    A = spin.generator(s, B)
+    import scipy.linalg
+    surv = np.array([np.mean([np.linalg.norm(scipy.linalg.expm(A * ti) @ p) ** 2 for p in psi0])
+                     for ti in t])
+    tol = TOL[prec]
+    assert np.max(np.abs(out[:, 0] - ps)) < tol
+    assert np.max(np.abs(out[:, 2] - surv)) < tol
+    assert np.max(np.abs(out[:, 1] - (surv - ps))) < tol
