@@ -254,6 +254,10 @@ def parse():
                     help="the paper's model problem (Table I couplings, Z = 2^20): Phi_S(B) at 21 "
                          "fields 0-10 mT with M = 200 (and the first 100 samples), the field of "
                          "the minimum, per-sample histograms at three fields; one JSON line")
+    ap.add_argument("--basis-sampling", action="store_true",
+                    help="config-2 system, 3 fields x 200 samples: spread of phi_S with "
+                         "coherent-state samples vs random basis states (deterministic = 2); "
+                         "one JSON line")
     ap.add_argument("--ncu-case3", action="store_true",
                     help="profiling case of the anisotropic config-3 system (Z = 2359296): "
                          "2 rows, two macro-steps, ~4 GB on the device")
@@ -389,6 +393,24 @@ def main():
                           "SE_plain_M2000": p["out"][:, 2].tolist(),
                           "z": z.tolist(), "chi2": float(np.sum(z ** 2)), "dof": len(idx),
                           "wall_plain_s": wall_plain}), flush=True)
+        return
+    if args.basis_sampling:
+        fb = w.fields[[1, 4, 12]]
+        res = {}
+        for name, det in (("coherent", 0), ("basis", 2)):
+            o = rp.rp_default_options(precision=prec, deterministic=det,
+                                      stream=torch.cuda.current_stream().cuda_stream)
+            t0 = time.perf_counter()
+            r = rp.rp_yields(sy.handle, fb, 200, 0, w.t_max, o, per_sample=True)
+            ps = r["per_sample"][:, :, 0]
+            res[name] = {"PhiS": ps.mean(1).round(6).tolist(),
+                         "sigma": ps.std(1, ddof=1).round(6).tolist(),
+                         "wall_s": time.perf_counter() - t0}
+        ratio = [(b / c) ** 2 for b, c in zip(res["basis"]["sigma"], res["coherent"]["sigma"])]
+        print(json.dumps({"mode": "basis-sampling", "workload": WORKLOAD, "fields_mT":
+                          [round(float(b), 4) for b in fb], "M": 200, **res,
+                          "variance_ratio_basis_over_coherent": [round(x, 3) for x in ratio]}),
+              flush=True)
         return
     if args.table1:
         gam = 176.085963023

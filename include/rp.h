@@ -75,7 +75,11 @@ typedef struct rp_options {
   double tol;             /* truncation bound per macro-step (0: 1e-15 FP64, 1e-9 FP32) */
   int max_rows;           /* concurrent propagations (0: from free device memory) */
   int deterministic;      /* 1: trace over the Z basis states |S, M> (Eq. 14)
-                             instead of M coherent-state samples; M is ignored */
+                             instead of M coherent-state samples; M is ignored.
+                             2: M basis states |S, M> drawn uniformly at random
+                             (rp_basis_indices) instead of coherent states, an
+                             unbiased estimate of the same trace (rp_yields and
+                             rp_time_trace only) */
   long long sample_offset;/* first sample index (resume / sharding) */
   uint32_t pair_id;       /* Philox counter word 3 (radical-pair id) */
   int profile;            /* 1: time the H.psi step kernels with CUDA events */
@@ -392,6 +396,14 @@ rp_status rp_yields_static(rp_system* sys, int n_fields, const double* fields, i
  * With t or out NULL only *n_times is set (a size query).
  * Errors: RP_EINVAL (max_times < n_times, M < 1, bad options), RP_ENOTCONV,
  * RP_ECUDA, RP_ENOMEM, RP_ENODEV. */
+/* Basis indices drawn by deterministic = 2 for samples sample_offset ..
+ * sample_offset + M - 1 (host only): Philox4x32-10 with counter
+ * (0xFFFFFFFF, s mod 2^32, s div 2^32, pair_id) and key (seed mod 2^32,
+ * seed div 2^32); u = ((x0 >> 5) 2^26 + (x1 >> 6)) / 2^53 and
+ * index = min(floor(u Z), Z - 1) in FP64.  out [M] host.  Errors: RP_EINVAL. */
+rp_status rp_basis_indices(uint64_t seed, uint32_t pair_id, long long sample_offset, int M,
+                           long long Z, long long* out);
+
 rp_status rp_time_trace(rp_system* sys, double B, int M, uint64_t seed, double t_max,
                         const rp_options* opt, int max_times, int* n_times, double* t,
                         double* out);

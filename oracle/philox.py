@@ -80,3 +80,22 @@ def draw_angles(seed: int, pair: int, samples, n_nuc: int):
     theta = np.arccos(1.0 - 2.0 * u1)
     phi = 2.0 * np.pi * u2
     return theta, phi
+
+
+def draw_basis_indices(seed: int, pair: int, samples, Z: int):
+    """Nuclear basis index of each sample for basis-state sampling (Eq. 14
+    sampled): counter (0xFFFFFFFF, s mod 2^32, s div 2^32, pair) -- word 0 is
+    never a nucleus index -- and the u1 map above; index = min(floor(u Z), Z - 1)."""
+    s = np.asarray(samples, dtype=np.uint64).reshape(-1)
+    ctr = np.zeros((s.size, 4), dtype=np.uint64)
+    ctr[:, 0] = np.uint64(0xFFFFFFFF)
+    ctr[:, 1] = s & _MASK
+    ctr[:, 2] = s >> np.uint64(32)
+    ctr[:, 3] = np.uint64(pair)
+    seed = int(seed)
+    key = np.zeros((s.size, 2), dtype=np.uint64)
+    key[:, 0] = np.uint64(seed & 0xFFFFFFFF)
+    key[:, 1] = np.uint64((seed >> 32) & 0xFFFFFFFF)
+    x = philox4x32_10(ctr, key)
+    u = uniform53(x[:, 0], x[:, 1])
+    return np.minimum(np.floor(u * float(Z)).astype(np.int64), int(Z) - 1)

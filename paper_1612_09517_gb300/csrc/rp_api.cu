@@ -555,9 +555,19 @@ int choose_rows(const rp::HostSystem& hs, const rp_options& o, int n_c, long lon
   return (int)std::max<long long>(1, std::min<long long>(items, cap));
 }
 
+// Sample identity of item s: 0 coherent-state sample index sample_offset + s;
+// 1 basis index s (the trace, Eq. 14); 2 a basis index drawn for sample
+// sample_offset + s (rp::basis_draw).
+struct SampleMode {
+  int mode = 0;
+  uint64_t seed = 0;
+  uint32_t pair = 0;
+  long long Z = 1;
+};
+
 std::vector<Item> make_items(const std::vector<rp::FieldPlan>& plans, const std::vector<long long>& first,
                              const std::vector<long long>& count, const std::vector<long long>& out0,
-                             long long sample_offset, bool deterministic,
+                             long long sample_offset, SampleMode sm,
                              const std::vector<int>* sys_of_field = nullptr) {
   // most expensive fields first, so that rows finish in waves
   std::vector<int> forder(plans.size());
@@ -567,8 +577,12 @@ std::vector<Item> make_items(const std::vector<rp::FieldPlan>& plans, const std:
   std::vector<Item> items;
   for (int f : forder)
     for (long long s = first[f]; s < first[f] + count[f]; ++s)
-      items.push_back(Item{f, deterministic ? s : sample_offset + s, out0[f] + (s - first[f]),
-                           (int)plans[f].n_macro, sys_of_field ? (*sys_of_field)[f] : 0});
+      items.push_back(Item{f,
+                           sm.mode == 1   ? s
+                           : sm.mode == 2 ? rp::basis_draw(sm.seed, sm.pair, sample_offset + s, sm.Z)
+                                          : sample_offset + s,
+                           out0[f] + (s - first[f]), (int)plans[f].n_macro,
+                           sys_of_field ? (*sys_of_field)[f] : 0});
   return items;
 }
 
@@ -636,13 +650,14 @@ rp_status run_yields(rp_system* sys, int n_fields, const double* fields, int M, 
   const double tol = o.tol > 0 ? o.tol : default_tol(o.precision);
   if (n_c % 4 != 0 || n_c < 8 || n_c > 88)
     return fail(RP_EINVAL, "n_cheb must be a multiple of 4 in [8, 88]");
-  const long long Mr = o.deterministic ? hs.Z : (long long)M;
+  const long long Mr = o.deterministic == 1 ? hs.Z : (long long)M;
   std::vector<rp::FieldPlan> plans;
   rp_status ps = plan_all(hs, n_fields, fields, t_max, n_c, tol, plans);
   if (ps != RP_OK) return ps;
   std::vector<long long> first(n_fields, 0), count(n_fields, Mr), out0(n_fields);
   for (int f = 0; f < n_fields; ++f) out0[f] = (long long)f * Mr;
-  const std::vector<Item> items = make_items(plans, first, count, out0, o.sample_offset, o.deterministic);
+  const std::vector<Item> items = make_items(plans, first, count, out0, o.sample_offset,
+                                             SampleMode{o.deterministic, seed, o.pair_id, hs.Z});
   const long long n_items = (long long)items.size();
   const int R = choose_rows<T>(hs, o, n_c, n_items);
 
@@ -692,12 +707,13 @@ rp_status run_time_trace(rp_system* sys, double B, int M, uint64_t seed, double 
   cudaStream_t st = (cudaStream_t)o.stream;
   const int n_c = o.n_cheb > 0 ? o.n_cheb : default_ncheb(o.precision);
   const double tol = o.tol > 0 ? o.tol : default_tol(o.precision);
-  const long long Mr = o.deterministic ? hs.Z : (long long)M;
+  const long long Mr = o.deterministic == 1 ? hs.Z : (long long)M;
   std::vector<rp::FieldPlan> plans;
   rp_status ps = plan_all(hs, 1, &B, t_max, n_c, tol, plans);
   if (ps != RP_OK) return ps;
   std::vector<long long> first(1, 0), count(1, Mr), out0(1, 0);
-  const std::vector<Item> items = make_items(plans, first, count, out0, o.sample_offset, o.deterministic);
+  const std::vector<Item> items = make_items(plans, first, count, out0, o.sample_offset,
+                                             SampleMode{o.deterministic, seed, o.pair_id, hs.Z});
   const int R = choose_rows<T>(hs, o, n_c, (long long)items.size());
   std::vector<double> h_tr(2 * (size_t)n_times, 0.0);
   {
@@ -769,7 +785,7 @@ rp_status run_converged(rp_system* sys, int n_fields, const double* fields, doub
         n += count[f];
       }
       if (n == 0) break;
-      const std::vector<Item> items = make_items(plans, first, count, out0, o.sample_offset, false);
+      const std::vector<Item> items = make_items(plans, first, count, out0, o.sample_offset, SampleMode{});
       double* d_ps = ar.get<double>((size_t)n * 3);
       eng.run(items, d_ps);
       std::vector<double> h((size_t)n * 3);
@@ -891,7 +907,7 @@ rp_status run_converged_cv(rp_system* sys, int n_fields, const double* fields, d
         n += count[f];
       }
       if (n == 0) return;
-      const std::vector<Item> items = make_items(plans, first, count, out0, 0, false);
+      const std::vector<Item> items = make_items(plans, first, count, out0, 0, SampleMode{});
       double* d_ps = ar.get<double>((size_t)n * 3);
       eng.run(items, d_ps);
       std::vector<double> h((size_t)n * 3);
@@ -1157,7 +1173,7 @@ rp_status run_batch(int n_sys, rp_system* const* systems, const int* n_fields,
         out0.push_back(base[s] + (long long)f * M[s]);
       }
     }
-    const std::vector<Item> items = make_items(gplans, first, count, out0, o.sample_offset, false,
+    const std::vector<Item> items = make_items(gplans, first, count, out0, o.sample_offset, SampleMode{},
                                                &sys_of_field);
     {
       Arena ar(st);
@@ -1396,7 +1412,8 @@ rp_status rp_yields(rp_system* s, int n_fields, const double* fields, int M, uin
   if (n_fields < 0) return fail(RP_EINVAL, "n_fields must be >= 0");
   if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
   if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..3, gram 0..2 and graph 0 or 1");
-  if (!o.deterministic && M < 2) return fail(RP_EINVAL, "M must be >= 2 (the standard error needs it)");
+  if (o.deterministic < 0 || o.deterministic > 2) return fail(RP_EINVAL, "deterministic must be 0, 1 or 2");
+  if (o.deterministic != 1 && M < 2) return fail(RP_EINVAL, "M must be >= 2 (the standard error needs it)");
   if (!(t_max > 0.0) || !std::isfinite(t_max)) return fail(RP_EINVAL, "t_max must be positive and finite");
   if (o.sample_offset < 0) return fail(RP_EINVAL, "sample_offset must be >= 0");
   if (n_fields > 0 && (!fields || !out)) return fail(RP_EINVAL, "NULL fields or out");
@@ -1417,6 +1434,15 @@ rp_status rp_yields(rp_system* s, int n_fields, const double* fields, int M, uin
   }
 }
 
+rp_status rp_basis_indices(uint64_t seed, uint32_t pair_id, long long sample_offset, int M,
+                           long long Z, long long* out) {
+  g_err.clear();
+  if (M < 0 || Z < 1 || sample_offset < 0) return fail(RP_EINVAL, "need M >= 0, Z >= 1, sample_offset >= 0");
+  if (M > 0 && !out) return fail(RP_EINVAL, "out is NULL");
+  for (int i = 0; i < M; ++i) out[i] = rp::basis_draw(seed, pair_id, sample_offset + i, Z);
+  return RP_OK;
+}
+
 rp_status rp_time_trace(rp_system* s, double B, int M, uint64_t seed, double t_max,
                         const rp_options* opt, int max_times, int* n_times, double* t,
                         double* out) {
@@ -1427,7 +1453,8 @@ rp_status rp_time_trace(rp_system* s, double B, int M, uint64_t seed, double t_m
   if (!s || !n_times) return fail(RP_EINVAL, "system or n_times is NULL");
   if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
   if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..3, gram 0..2 and graph 0 or 1");
-  if (!o.deterministic && M < 1) return fail(RP_EINVAL, "M must be >= 1");
+  if (o.deterministic < 0 || o.deterministic > 2) return fail(RP_EINVAL, "deterministic must be 0, 1 or 2");
+  if (o.deterministic != 1 && M < 1) return fail(RP_EINVAL, "M must be >= 1");
   if (!(t_max > 0.0) || !std::isfinite(t_max)) return fail(RP_EINVAL, "t_max must be positive and finite");
   if (!std::isfinite(B)) return fail(RP_EINVAL, "non-finite field");
   if (o.sample_offset < 0) return fail(RP_EINVAL, "sample_offset must be >= 0");

@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <atomic>
+
 namespace rp {
 namespace {
 
@@ -43,6 +45,22 @@ __device__ double block_sum(double v, double* sh) {
     __syncthreads();
   }
   return sh[0];
+}
+
+// cudaFuncSetAttribute(MaxDynamicSharedMemorySize) for `func` once per
+// device (the attribute belongs to the current device); `done` is the call
+// site's bit mask of devices already set.  Repeating the call from several
+// host threads is harmless.
+inline cudaError_t smem_attr_once(const void* func, int bytes,
+                                  std::atomic<unsigned long long>& done) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const unsigned long long bit = dev < 64 ? 1ull << dev : 0ull;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+  return e;
 }
 
 }  // namespace

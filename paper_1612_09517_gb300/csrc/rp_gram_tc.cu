@@ -388,13 +388,9 @@ cudaError_t launch_gram_tc(const float* X, const double* W, const int* row_field
   if (rows == 0) return cudaSuccess;
   if (!gram_tc_supported(n_c)) return cudaErrorInvalidValue;
   const size_t smem = gram_tc_smem_bytes(n_c);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_max_gram_tc());
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static std::atomic<unsigned long long> attr_done;
+  const cudaError_t ea = smem_attr_once((const void*)k_gram_tc, (int)smem_max_gram_tc(), attr_done);
+  if (ea != cudaSuccess) return ea;
   // chunks per CTA: the split of each row that minimises (waves of resident
   // CTAs) x (chunks per CTA + a fixed cost for fill and epilogue)
   const long long n_chunks = (Zs + kXChunk - 1) / kXChunk;

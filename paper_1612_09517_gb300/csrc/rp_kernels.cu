@@ -1327,14 +1327,10 @@ cudaError_t launch_step(const SysTab<T>& S, const HamDev<T>* one, int aniso, int
     const HamDev<float>& hf = *reinterpret_cast<const HamDev<float>*>(one);
     const size_t smem = (size_t)(1 + bulk_max_partner_tiles(hf)) * kBulkTileBytes;
     if (smem <= (size_t)kBulkMaxSmem) {
-      static bool attr_set[2] = {false, false};
+      static std::atomic<unsigned long long> attr_done[2];
       auto kf = aniso ? k_cheb_step_bulk<true> : k_cheb_step_bulk<false>;
-      if (!attr_set[aniso ? 1 : 0]) {
-        cudaError_t e = cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kBulkMaxSmem);
-        if (e != cudaSuccess) return e;
-        attr_set[aniso ? 1 : 0] = true;
-      }
+      const cudaError_t e = smem_attr_once((const void*)kf, kBulkMaxSmem, attr_done[aniso ? 1 : 0]);
+      if (e != cudaSuccess) return e;
       dim3 grid((unsigned)(one->Z / kBulkTile), rows);
       kf<<<grid, kBulkTile, smem, st>>>(
           S_as_float(S), hf, reinterpret_cast<const FieldDev<float>*>(fields), row_field, row_win,

@@ -314,4 +314,37 @@ std::string plan_field(const HostSystem& s, double B_mT, double t_max, int n_c, 
   return "";
 }
 
+namespace {
+
+// One Philox4x32-10 block (ten rounds; multipliers and Weyl key increments of
+// the published generator).
+void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u, W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  for (int round = 0; round < 10; ++round) {
+    const uint64_t p0 = (uint64_t)M0 * c[0], p1 = (uint64_t)M1 * c[2];
+    const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+    c[0] = n0;
+    c[1] = lo1;
+    c[2] = n2;
+    c[3] = lo0;
+    k0 += W0;
+    k1 += W1;
+  }
+}
+
+}  // namespace
+
+long long basis_draw(uint64_t seed, uint32_t pair, long long sample, long long Z) {
+  uint32_t c[4] = {0xFFFFFFFFu, (uint32_t)((uint64_t)sample & 0xFFFFFFFFu),
+                   (uint32_t)((uint64_t)sample >> 32), pair};
+  philox4x32_10(c, (uint32_t)(seed & 0xFFFFFFFFu), (uint32_t)(seed >> 32));
+  const double u = ((double)(c[0] >> 5) * 67108864.0 + (double)(c[1] >> 6)) *
+                   (1.0 / 9007199254740992.0);
+  long long idx = (long long)std::floor(u * (double)Z);
+  if (idx > Z - 1) idx = Z - 1;
+  return idx;
+}
+
 }  // namespace rp

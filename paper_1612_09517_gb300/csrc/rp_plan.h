@@ -12,6 +12,8 @@
 // which this file evaluates by Gauss-Legendre quadrature.
 #pragma once
 
+#include <cstdint>
+
 #include <complex>
 #include <string>
 #include <vector>
@@ -69,5 +71,14 @@ std::string finish_system(HostSystem& s);
 // Plan one field.  Returns an empty string on success or an error message.
 std::string plan_field(const HostSystem& s, double B_mT, double t_max, int n_cheb, double tol,
                        bool want_coef, FieldPlan* out);
+
+// Nuclear basis index of sample `sample` for basis-state sampling (Eq. 14
+// sampled instead of summed): Philox4x32-10 (Salmon et al., SC'11) with
+// counter (0xFFFFFFFF, sample mod 2^32, sample div 2^32, pair) and key
+// (seed mod 2^32, seed div 2^32) -- counter word 0 is never a nucleus index,
+// so these draws are disjoint from the coherent-state angles -- then
+// u = ((x0 >> 5) 2^26 + (x1 >> 6)) / 2^53 and index = min(floor(u Z), Z - 1)
+// in FP64.
+long long basis_draw(uint64_t seed, uint32_t pair, long long sample, long long Z);
 
 }  // namespace rp

@@ -348,6 +348,7 @@ extern "C" rp_status rp_yields_static(rp_system* s, int n_fields, const double* 
   if (!s) return sfail(RP_EINVAL, "system is NULL");
   if (n_fields < 0) return sfail(RP_EINVAL, "n_fields must be >= 0");
   if (o.precision != RP_FP64 && o.precision != RP_FP32) return sfail(RP_EINVAL, "bad precision");
+  if (o.deterministic > 1) return sfail(RP_ENOTIMPL, "basis-state sampling (deterministic = 2) is served by rp_yields");
   if (!o.deterministic && M < 2) return sfail(RP_EINVAL, "M must be >= 2 (the standard error needs it)");
   if (!(t_max > 0.0) || !std::isfinite(t_max)) return sfail(RP_EINVAL, "t_max must be positive and finite");
   if (o.sample_offset < 0) return sfail(RP_EINVAL, "sample_offset must be >= 0");

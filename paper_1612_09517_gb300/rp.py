@@ -140,6 +140,8 @@ SIGNATURES = [
                                    C.c_uint64, C.c_double, C.POINTER(rp_options),
                                    C.POINTER(C.c_double), C.POINTER(C.c_double),
                                    C.POINTER(rp_stats)]),
+    ("rp_basis_indices", C.c_int, [C.c_uint64, C.c_uint32, C.c_longlong, C.c_int, C.c_longlong,
+                                   C.POINTER(C.c_longlong)]),
     ("rp_time_trace", C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_uint64, C.c_double,
                                 C.POINTER(rp_options), C.c_int, C.POINTER(C.c_int),
                                 C.POINTER(C.c_double), C.POINTER(C.c_double)]),
@@ -228,7 +230,7 @@ def rp_yields(h, fields, M, seed, t_max, opt=None, per_sample=False, Z=None):
     nf = fields.size
     o = opt if opt is not None else rp_default_options()
     out = np.zeros(max(nf * 5, 1))
-    Mr = Z if o.deterministic else M
+    Mr = Z if o.deterministic == 1 else M
     ps = np.zeros(max(nf * Mr * 3, 1)) if per_sample else None
     stats = rp_stats()
     _check(LIB.rp_yields(h, nf, _dptr(fields), int(M), C.c_uint64(int(seed)), float(t_max),
@@ -261,7 +263,7 @@ def rp_yields_static(h, fields, M, seed, t_max, opt=None, per_sample=False, Z=No
     nf = fields.size
     o = opt if opt is not None else rp_default_options()
     out = np.zeros(max(nf * 5, 1))
-    Mr = Z if o.deterministic else M
+    Mr = Z if o.deterministic == 1 else M
     ps = np.zeros(max(nf * Mr * 3, 1)) if per_sample else None
     stats = rp_stats()
     _check(LIB.rp_yields_static(h, nf, _dptr(fields), int(M), C.c_uint64(int(seed)),
@@ -271,6 +273,14 @@ def rp_yields_static(h, fields, M, seed, t_max, opt=None, per_sample=False, Z=No
     if per_sample:
         res["per_sample"] = ps[: nf * Mr * 3].reshape(nf, Mr, 3)
     return res
+
+
+def rp_basis_indices(seed, pair_id, sample_offset, M, Z):
+    """Basis indices of deterministic = 2 (host only)."""
+    out = np.zeros(max(int(M), 1), dtype=np.int64)
+    _check(LIB.rp_basis_indices(C.c_uint64(int(seed)), C.c_uint32(int(pair_id)), int(sample_offset),
+                                int(M), int(Z), out.ctypes.data_as(C.POINTER(C.c_longlong))))
+    return out[: int(M)]
 
 
 def rp_time_trace(h, B, M, seed, t_max, opt=None):

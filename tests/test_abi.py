@@ -158,3 +158,14 @@ def test_time_trace_size_query_and_capacity():
     st = rp.LIB.rp_time_trace(sy.handle, 1.5, 4, ctypes.c_uint64(0), 2.0, ctypes.byref(o),
                               n.value - 1, ctypes.byref(n), dp(t), dp(out))
     assert st == 1  # RP_EINVAL
+
+
+def test_basis_indices_bit_exact_with_oracle():
+    """The library's host draw of basis indices (deterministic = 2) equals the
+    oracle's Philox draw bit for bit."""
+    from oracle import philox
+    for seed, pair, off, Z in ((0, 0, 0, 16), (12345678901, 7, 2 ** 33 + 5, 20736),
+                               (3, 1, 1000, 1048576), (2 ** 63 + 11, 2 ** 31, 17, 3)):
+        got = rp.rp_basis_indices(seed, pair, off, 64, Z)
+        ref = philox.draw_basis_indices(seed, pair, np.arange(off, off + 64, dtype=np.uint64), Z)
+        assert np.array_equal(got, ref), (seed, pair, off, Z)

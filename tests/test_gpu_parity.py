@@ -486,3 +486,28 @@ def test_time_trace_matches_dense_oracle(prec):
     assert np.max(np.abs(out[:, 0] - ps)) < tol
     assert np.max(np.abs(out[:, 2] - surv)) < tol
     assert np.max(np.abs(out[:, 1] - (surv - ps))) < tol
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_basis_state_sampling_matches_oracle(prec):
+    """deterministic = 2: M basis states |S, M> drawn at random; per-sample
+    yields equal the oracle's for the same drawn indices, and the draw is the
+    library's own rp_basis_indices."""
+    from oracle import philox
+    rp = _rp()
+    s = wl.random_isotropic(3, 1, two_I=[1, 2, 1, 1], k_S=2.0, k_T=0.5, J=0.2, seed=54)
+    sy = rp.System(s)
+    M, B, T = 6, 1.5, 1.0
+    r = sy.yields([B], M, 21, T, per_sample=True, precision=prec, deterministic=2, pair_id=4,
+                  sample_offset=10)
+    idx = philox.draw_basis_indices(21, 4, np.arange(10, 10 + M), s.Z)
+    assert np.array_equal(idx, rp.rp_basis_indices(21, 4, 10, M, s.Z))
+    # |S> x |m> in the library layout (configuration m, electron index e = 2 e1 + e2
+    # innermost: <S| = (<ab| - <ba|)/sqrt 2), then in the oracle's kron order
+    lib = np.zeros((M, 4 * s.Z), complex)
+    for k, m in enumerate(idx):
+        lib[k, 4 * m + 1], lib[k, 4 * m + 2] = 2 ** -0.5, -(2 ** -0.5)
+    psi0 = sy.to_input_order(lib)
+    assert np.allclose(np.abs(psi0 @ coherent.basis_states(s).conj().T).max(axis=1), 1.0)
+    phS, phT, surv = dense.sample_yields(s, B, T, psi0)
+    _cmp_per_sample(r["per_sample"][0], phS, phT, surv, prec)

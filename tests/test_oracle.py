@@ -396,3 +396,19 @@ def test_resonance_minimum_at_omega_2J():
     Bs = np.linspace(0.0, 4.0, 41)
     phi = np.array([dense.trace_yields(s, B, 3.0)[0] for B in Bs])
     assert abs(Bs[np.argmin(phi)] - 2.0) <= 0.2
+
+
+def test_basis_index_draw_is_uniform_and_disjoint_from_angles():
+    """Basis-state sampling draws: every index in range, uniform over Z bins
+    (chi-square at the 1e-4 level), and a different stream from the angles
+    (counter word 0 is 0xFFFFFFFF, never a nucleus index)."""
+    from oracle import philox
+    Z = 48
+    idx = philox.draw_basis_indices(5, 3, np.arange(96000), Z)
+    assert idx.min() >= 0 and idx.max() <= Z - 1
+    counts = np.bincount(idx, minlength=Z)
+    exp = idx.size / Z
+    chi2 = float(np.sum((counts - exp) ** 2 / exp))
+    assert chi2 < 100.0  # 47 dof: P(chi2 > 100) < 1e-5
+    u1, _ = philox.draw_uniforms(5, 3, np.arange(8), 1)
+    assert not np.array_equal(np.floor(u1[:, 0] * Z).astype(np.int64), idx[:8])
