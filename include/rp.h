@@ -377,7 +377,9 @@ rp_status rp_yields_cv(rp_system* sys, int n_fields, const double* fields, doubl
  * it (the call clears what must start at zero); calls that overlap on the GPU
  * race on it.  The first call on a device looks up the array's address with
  * that device current and should come before any stream capture.
- * rp_stats.device_ms and the step timings are not measured (0). */
+ * rp_stats.device_ms and the step timings are not measured (0).
+ * opt->deterministic = 2 (random basis states) is not served here
+ * (RP_ENOTIMPL); 0 and 1 are. */
 rp_status rp_yields_static(rp_system* sys, int n_fields, const double* fields, int M,
                            uint64_t seed, double t_max, const rp_options* opt, double* out,
                            double* per_sample, rp_stats* stats);
