@@ -169,3 +169,20 @@ def test_basis_indices_bit_exact_with_oracle():
         got = rp.rp_basis_indices(seed, pair, off, 64, Z)
         ref = philox.draw_basis_indices(seed, pair, np.arange(off, off + 64, dtype=np.uint64), Z)
         assert np.array_equal(got, ref), (seed, pair, off, Z)
+
+
+def test_option_validation_without_gpu():
+    """Execution options outside their ranges are refused before any device
+    work: kernel path, time-integral path, graph replay, sampling mode; the
+    autotuner needs two rows; basis-index draws need a positive Z."""
+    sy = rp.System(wl.config1().system)
+    for kw, msg in ((dict(kernel=4), "kernel"), (dict(kernel=-1), "kernel"), (dict(gram=3), "gram"),
+                    (dict(graph=2), "graph"), (dict(deterministic=3), "deterministic")):
+        with pytest.raises(rp.RPError, match=msg):
+            sy.yields([0.0], 4, 0, 1.0, **kw)
+    with pytest.raises(rp.RPError, match="rows"):
+        rp.rp_tune(sy.handle, 1.0, 1)
+    with pytest.raises(rp.RPError, match="RP_EINVAL"):
+        rp.rp_basis_indices(0, 0, 0, 4, 0)
+    with pytest.raises(rp.RPError, match="coherent"):
+        sy.yields_converged([0.0], 1e-3, 8, 100, 0, 1.0, deterministic=1)
