@@ -121,6 +121,26 @@ def test_philox_weyl_constants():
     assert philox.PHILOX_W1 == int((Decimal(3).sqrt() - 1) * (1 << 32))
 
 
+def test_philox_known_answer_vectors():
+    """Known-answer vectors of Philox4x32-10 published with the Random123
+    library of Salmon et al. (SC'11): (counter, key) -> four output words.
+    A wrong multiplier, a wrong Weyl constant, a missing round or swapped
+    output words each change all of them."""
+    kat = [
+        ((0, 0, 0, 0), (0, 0), (0x6627E8D5, 0xE169C58D, 0xBC57AC4C, 0x9B00DBD8)),
+        ((0xFFFFFFFF,) * 4, (0xFFFFFFFF,) * 2, (0x408F276D, 0x41C83B0E, 0xA20BC7C6, 0x6D5451FD)),
+        ((0x243F6A88, 0x85A308D3, 0x13198A2E, 0x03707344), (0xA4093822, 0x299F31D0),
+         (0xD16CFE09, 0x94FDCCEB, 0x5001E420, 0x24126EA1)),
+    ]
+    for ctr, key, want in kat:
+        got = philox.philox4x32_10(np.array(ctr, dtype=np.uint64), np.array(key, dtype=np.uint64))
+        assert [int(x) for x in got] == list(want), (ctr, key, [hex(int(x)) for x in got])
+    # vectorised form gives the same words
+    c = np.array([k[0] for k in kat], dtype=np.uint64)
+    k = np.array([k[1] for k in kat], dtype=np.uint64)
+    assert np.array_equal(philox.philox4x32_10(c, k), np.array([k_[2] for k_ in kat], dtype=np.uint64))
+
+
 def test_philox_round_is_bijective_on_sample():
     """Distinct counters give distinct outputs (Philox is a keyed bijection)."""
     rng = np.random.default_rng(0)
