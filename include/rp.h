@@ -28,7 +28,7 @@
  *   - An rp_system is owned by the library from rp_create to rp_destroy.
  *     Calls on one system are not thread-safe.
  *   - Compute entry points run on the CUDA stream given in rp_options.stream
- *     (or the per-thread default stream when NULL) and synchronise that
+ *     (or the legacy default stream when NULL) and synchronise that
  *     stream before returning, so host outputs are complete on return.
  *
  * State vector layout (rp_apply_h, rp_init_states): complex interleaved
@@ -83,7 +83,7 @@ typedef struct rp_options {
   long long sample_offset;/* first sample index (resume / sharding) */
   uint32_t pair_id;       /* Philox counter word 3 (radical-pair id) */
   int profile;            /* 1: time the H.psi step kernels with CUDA events */
-  void* stream;           /* cudaStream_t, NULL: per-thread default stream */
+  void* stream;           /* cudaStream_t, NULL: the legacy default stream */
   int kernel;             /* 0: choose; 1: one launch per Chebyshev term (any Z);
                              2: a whole macro-step per launch with each row's
                              vectors in shared memory (Z <= 2048 FP32, 1024
@@ -276,7 +276,7 @@ typedef struct rp_cv_options {
   double weight_decay;   /* decoupled weight decay (default 1e-4) */
   double B_scale;        /* field scale of the last feature, mT (default 10) */
   uint64_t init_seed;    /* weight initialisation and shuffling seed (default 1) */
-  void* stream;          /* cudaStream_t, NULL: per-thread default stream */
+  void* stream;          /* cudaStream_t, NULL: the legacy default stream */
 } rp_cv_options;
 
 /* Defaults above. */
@@ -376,10 +376,14 @@ rp_status rp_yields_cv(rp_system* sys, int n_fields, const double* fields, doubl
  * needs.  All calls share the array and find the previous call's contents in
  * it (the call clears what must start at zero); calls that overlap on the GPU
  * race on it.  The first call on a device looks up the array's address with
- * that device current and should come before any stream capture.
+ * that device current and should come before any stream capture; the
+ * address is kept for the life of the process, so after a cudaDeviceReset of
+ * that device this entry point must not be called there again.
  * rp_stats.device_ms and the step timings are not measured (0).
- * opt->deterministic = 2 (random basis states) is not served here
- * (RP_ENOTIMPL); 0 and 1 are. */
+ * It always runs the per-term kernels (kernel = 1) with the CUDA-core time
+ * integral (gram = 1), eagerly: kernel and gram other than 0 or 1, graph
+ * other than 0, and opt->deterministic = 2 (random basis states) are refused
+ * with RP_ENOTIMPL; max_rows > 0 caps the rows of a batch. */
 rp_status rp_yields_static(rp_system* sys, int n_fields, const double* fields, int M,
                            uint64_t seed, double t_max, const rp_options* opt, double* out,
                            double* per_sample, rp_stats* stats);

@@ -18,7 +18,9 @@
 // at zero.  Calls that overlap on the GPU (other streams, other host threads)
 // race on the array.  The first call on a device looks up the array's device
 // address (cudaGetSymbolAddress, with that device current); that first call
-// should come before any stream capture.
+// should come before any stream capture.  The address is kept for the life of
+// the process: a caller that resets the device (cudaDeviceReset) must not call
+// this entry point on that device afterwards.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -190,7 +192,8 @@ rp_status run_static(const rp::HostSystem& hs, int n_fields, const double* field
                                 " bytes of scratch for this workload; the static array holds " +
                                 std::to_string(kStaticScratchBytes) + " bytes");
   size_t R = 1;
-  while (R < (size_t)items && R < 65535 && fixed + rows_bytes(R + 1) <= kStaticScratchBytes) ++R;
+  const size_t R_cap = o.max_rows > 0 ? std::min<size_t>((size_t)o.max_rows, 65535) : 65535;
+  while (R < (size_t)items && R < R_cap && fixed + rows_bytes(R + 1) <= kStaticScratchBytes) ++R;
 
   Bump b{scratch};
   double* d_ps = b.get<double>((size_t)items * 3);
@@ -348,7 +351,14 @@ extern "C" rp_status rp_yields_static(rp_system* s, int n_fields, const double* 
   if (!s) return sfail(RP_EINVAL, "system is NULL");
   if (n_fields < 0) return sfail(RP_EINVAL, "n_fields must be >= 0");
   if (o.precision != RP_FP64 && o.precision != RP_FP32) return sfail(RP_EINVAL, "bad precision");
+  if (o.deterministic < 0 || o.deterministic > 2) return sfail(RP_EINVAL, "deterministic must be 0, 1 or 2");
   if (o.deterministic > 1) return sfail(RP_ENOTIMPL, "basis-state sampling (deterministic = 2) is served by rp_yields");
+  // this entry point runs the per-term kernels with the CUDA-core integral,
+  // eagerly: other launch choices are refused rather than silently ignored
+  if (o.kernel != 0 && o.kernel != 1) return sfail(RP_ENOTIMPL, "rp_yields_static runs kernel = 1 only (0 or 1 accepted)");
+  if (o.gram != 0 && o.gram != 1) return sfail(RP_ENOTIMPL, "rp_yields_static runs gram = 1 only (0 or 1 accepted)");
+  if (o.graph != 0) return sfail(RP_ENOTIMPL, "rp_yields_static does not replay CUDA graphs (graph must be 0)");
+  if (o.max_rows < 0) return sfail(RP_EINVAL, "max_rows must be >= 0");
   if (!o.deterministic && M < 2) return sfail(RP_EINVAL, "M must be >= 2 (the standard error needs it)");
   if (!(t_max > 0.0) || !std::isfinite(t_max)) return sfail(RP_EINVAL, "t_max must be positive and finite");
   if (o.sample_offset < 0) return sfail(RP_EINVAL, "sample_offset must be >= 0");

@@ -186,3 +186,15 @@ def test_option_validation_without_gpu():
         rp.rp_basis_indices(0, 0, 0, 4, 0)
     with pytest.raises(rp.RPError, match="coherent"):
         sy.yields_converged([0.0], 1e-3, 8, 100, 0, 1.0, deterministic=1)
+
+
+def test_static_entry_point_refuses_other_launch_choices_without_gpu():
+    """rp_yields_static always runs the per-term kernels with the CUDA-core
+    integral, eagerly: other kernel, gram and graph choices, and random
+    basis-state sampling, are refused before any device work."""
+    sy = rp.System(wl.config1().system)
+    for kw, msg in ((dict(kernel=2), "kernel"), (dict(kernel=3), "kernel"), (dict(gram=2), "gram"),
+                    (dict(graph=1), "graph"), (dict(deterministic=2), "basis-state"),
+                    (dict(max_rows=-1), "max_rows")):
+        with pytest.raises(rp.RPError, match=msg):
+            rp.rp_yields_static(sy.handle, [0.0], 4, 0, 1.0, rp.rp_default_options(**kw))

@@ -55,6 +55,26 @@ def test_static_scratch_matches_allocating_entry_point(prec):
         assert a["stats"]["kernel_launches"] > 0 and a["stats"]["rows"] >= 1
 
 
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_static_scratch_deterministic_trace_matches(prec):
+    """The deterministic trace over the Z = 16 basis states of config 1 (Eq. 14)
+    through the allocation-free entry point equals rp_yields, twice in a row,
+    the second time with the rows capped at 5 (ten batches through the array)."""
+    from paper_1612_09517_gb300 import rp
+    s = wl.config1().system
+    sy = rp.System(s)
+    fields = np.array([0.0, 1.5, 5.0])
+    for max_rows in (0, 5):
+        o = rp.rp_default_options(precision=prec, deterministic=1, max_rows=max_rows)
+        a = rp.rp_yields_static(sy.handle, fields, 2, 0, 2.0, o, per_sample=True, Z=sy.Z)
+        b = rp.rp_yields(sy.handle, fields, 2, 0, 2.0, o, per_sample=True, Z=sy.Z)
+        assert a["per_sample"].shape == (3, sy.Z, 3)
+        assert _close(a["per_sample"], b["per_sample"], prec)
+        assert _close(a["out"], b["out"], prec)
+        if max_rows:
+            assert a["stats"]["rows"] == max_rows
+
+
 def test_static_scratch_rejects_oversized_workload():
     from paper_1612_09517_gb300 import rp
     s = wl.random_isotropic(9, 9, seed=1)  # Z = 2^18: one FP32 row needs > 64 MiB
