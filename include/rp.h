@@ -91,7 +91,13 @@ typedef struct rp_options {
                              single systems with >= 8 spin-1/2 nuclei stage
                              each block's partner configurations with bulk
                              async copies (slower than 1 on the workloads
-                             measured so far; a candidate of rp_tune) */
+                             measured so far; a candidate of rp_tune);
+                             4: a whole macro-step per launch on a cluster of
+                             2^c CTAs per row (c <= 3) holding the row's
+                             Chebyshev vectors in distributed shared memory
+                             (FP32, one isotropic system with Z / 2^c <= 3520,
+                             2^c <= 2^(number of spin-1/2 nuclei); otherwise
+                             falls back to 1) */
   int gram;               /* time integral (Eqs. 20, 22) of each macro-step: 0 choose
                              (2 where it applies); 1 CUDA cores (any precision);
                              2 tensor cores (FP32 single systems with the

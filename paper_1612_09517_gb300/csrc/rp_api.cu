@@ -157,7 +157,7 @@ rp::LayoutDev make_layout(const rp::HostSystem& s) {
 int default_ncheb(int) { return 88; }  // fastest measured in both precisions (rp_tune)
 
 bool bad_kernel_choice(const rp_options& o) {
-  return o.kernel < 0 || o.kernel > 3 || o.graph < 0 || o.graph > 1 || o.gram < 0 || o.gram > 2;
+  return o.kernel < 0 || o.kernel > 4 || o.graph < 0 || o.graph > 1 || o.gram < 0 || o.gram > 2;
 }
 double default_tol(int precision) { return precision == RP_FP64 ? 1e-15 : 1e-9; }
 
@@ -267,6 +267,13 @@ class YieldEngine {
     row_sys_ = ar_.get<int>(R);
     small_ = (o_.kernel == 2 || (o_.kernel == 0 && Zslot_ <= rp::small_max_configs<T>())) &&
              Zslot_ <= rp::small_max_configs<T>();
+    // a whole macro-step per launch on a thread-block cluster per row (FP32,
+    // one isotropic system whose state fits the cluster's shared memory)
+    cluster_ = false;
+    if (sizeof(T) == 4 && !small_ && sys_.size() == 1 && o_.kernel == 4) {
+      const auto& hf = *reinterpret_cast<const rp::HamDev<float>*>(&ham1_);
+      cluster_ = rp::macro_cluster_plan(hf, nullptr) && rp::macro_cluster_max_active(hf) > 0;
+    }
     // tensor-core time integral: FP32 with the per-term kernels (each row's
     // integral covers its own system's Z; the step kernel keeps the padding of
     // the last 16-configuration chunk at zero)
@@ -355,7 +362,7 @@ class YieldEngine {
         ck(cudaEventRecord(a, st_), "cudaEventRecord");
       }
       double bytes = 0.0;
-      if (small_) {
+      if (small_ || cluster_) {
         // the whole macro-step on chip: HBM traffic is psi in, psi out and the singlet slices
         bytes = (2.0 + 0.25 * n_c_) * vbytes;
       } else {
@@ -458,7 +465,18 @@ class YieldEngine {
          "macro-step kernel");
       n_step = 1;
     }
-    for (int n = 1; n < n_c_ && !small_; ++n) {
+    if (cluster_) {
+      ck(rp::launch_macro_cluster(*reinterpret_cast<const rp::HamDev<float>*>(&ham1_),
+                                  reinterpret_cast<const rp::FieldDev<float>*>(d_fdev_),
+                                  rows_.field, rows_.win, k, mdev, R_,
+                                  reinterpret_cast<const float*>(P), reinterpret_cast<float*>(Q),
+                                  reinterpret_cast<float*>(X_),
+                                  reinterpret_cast<const float*>(d_coef_), n_c_, Zslot_,
+                                  tc_gram_ ? 1 : 0, s),
+         "cluster macro-step kernel");
+      n_step = 1;
+    }
+    for (int n = 1; n < n_c_ && !small_ && !cluster_; ++n) {
       const int mode = (n == 1) ? rp::MODE_FIRST : (n == n_c_ - 1 ? rp::MODE_LAST : rp::MODE_MID);
       ck(rp::launch_step<T>(S_, one, aniso_, o_.kernel == 3, d_fdev_, rows_.field, rows_.win, k, mdev, R_,
                             phi[(n - 1) % 3], n >= 2 ? phi[(n - 2) % 3] : nullptr,
@@ -529,6 +547,7 @@ class YieldEngine {
   uint32_t* d_pair_ = nullptr;
   rp::HamDev<T> ham1_{};
   bool small_ = false;
+  bool cluster_ = false;
   bool tc_gram_ = false;
   int n_sm_ = 0;
   rp::SysTab<T> S_{};
@@ -1411,7 +1430,7 @@ rp_status rp_yields(rp_system* s, int n_fields, const double* fields, int M, uin
   if (!s) return fail(RP_EINVAL, "system is NULL");
   if (n_fields < 0) return fail(RP_EINVAL, "n_fields must be >= 0");
   if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
-  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..3, gram 0..2 and graph 0 or 1");
+  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..4, gram 0..2 and graph 0 or 1");
   if (o.deterministic < 0 || o.deterministic > 2) return fail(RP_EINVAL, "deterministic must be 0, 1 or 2");
   if (o.deterministic != 1 && M < 2) return fail(RP_EINVAL, "M must be >= 2 (the standard error needs it)");
   if (!(t_max > 0.0) || !std::isfinite(t_max)) return fail(RP_EINVAL, "t_max must be positive and finite");
@@ -1452,7 +1471,7 @@ rp_status rp_time_trace(rp_system* s, double B, int M, uint64_t seed, double t_m
   else rp_default_options(&o);
   if (!s || !n_times) return fail(RP_EINVAL, "system or n_times is NULL");
   if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
-  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..3, gram 0..2 and graph 0 or 1");
+  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..4, gram 0..2 and graph 0 or 1");
   if (o.deterministic < 0 || o.deterministic > 2) return fail(RP_EINVAL, "deterministic must be 0, 1 or 2");
   if (o.deterministic != 1 && M < 1) return fail(RP_EINVAL, "M must be >= 1");
   if (!(t_max > 0.0) || !std::isfinite(t_max)) return fail(RP_EINVAL, "t_max must be positive and finite");
@@ -1492,7 +1511,7 @@ rp_status rp_yields_converged(rp_system* s, int n_fields, const double* fields, 
   if (!s) return fail(RP_EINVAL, "system is NULL");
   if (n_fields < 0) return fail(RP_EINVAL, "n_fields must be >= 0");
   if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
-  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..3, gram 0..2 and graph 0 or 1");
+  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..4, gram 0..2 and graph 0 or 1");
   if (o.deterministic) return fail(RP_EINVAL, "rp_yields_converged samples coherent states only");
   if (!(se_target > 0.0) || !std::isfinite(se_target)) return fail(RP_EINVAL, "se_target must be positive");
   if (M_min < 2 || M_max < M_min) return fail(RP_EINVAL, "need 2 <= M_min <= M_max");
@@ -1541,7 +1560,7 @@ rp_status rp_yields_cv(rp_system* s, int n_fields, const double* fields, double 
   if (!s) return fail(RP_EINVAL, "system is NULL");
   if (n_fields < 0) return fail(RP_EINVAL, "n_fields must be >= 0");
   if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
-  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..3, gram 0..2 and graph 0 or 1");
+  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..4, gram 0..2 and graph 0 or 1");
   if (o.deterministic) return fail(RP_EINVAL, "rp_yields_cv samples coherent states only");
   if (!(se_target > 0.0) || !std::isfinite(se_target)) return fail(RP_EINVAL, "se_target must be positive");
   if (M_min < 2 || M_max < M_min) return fail(RP_EINVAL, "need 2 <= M_min <= M_max");
@@ -1581,7 +1600,7 @@ rp_status rp_yields_batch(int n_sys, rp_system* const* systems, const int* n_fie
   if (n_sys == 0) return RP_OK;
   if (!systems || !n_fields || !fields || !M || !t_max || !out) return fail(RP_EINVAL, "NULL argument");
   if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
-  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..3, gram 0..2 and graph 0 or 1");
+  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..4, gram 0..2 and graph 0 or 1");
   if (o.deterministic) return fail(RP_EINVAL, "rp_yields_batch samples coherent states only");
   if (o.sample_offset < 0) return fail(RP_EINVAL, "sample_offset must be >= 0");
   long long total = 0;

@@ -908,6 +908,290 @@ __global__ void __launch_bounds__(256) k_macro_small(
   }
 }
 
+// ---- whole macro-steps of mid-size systems on a thread-block cluster ----
+// For an isotropic FP32 system whose state splits over C = 2^c CTAs of one
+// cluster (c <= kClusterMaxBits) with Zl = Z / C <= kClusterMaxLocal
+// configurations per CTA, the cluster holds a row's phi_{n-1} and phi_n in
+// distributed shared memory for a whole macro-step: HBM sees psi in, psi out
+// and the singlet slices only.  The CTA rank is the value of the c outermost
+// spin-1/2 nuclei (layout positions lb .. n_half - 1, lb = n_half - c), so the
+// configuration m of local index l is
+//   m = ((l >> lb) << (lb + c)) | (rank << lb) | (l & (2^lb - 1)),
+// and the partners of H.psi (Eq. 1, isotropic flip-flops) are
+//   spin-1/2 at p < lb:       l XOR 2^p in this CTA,
+//   spin-1/2 at lb + i:       the same l in CTA rank XOR 2^i (ld.shared::cluster),
+//   higher spins (p >= n_half): l +- stride_p / C in this CTA.
+// Shared memory per buffer: four planes of Zl complex values, one per electron
+// state e, so a flip-flop partner (two of the four components) costs two
+// contiguous 8-byte reads per thread.  Each thread owns the KPT local
+// configurations l = tid + j NT; the accumulator psi(h) = sum_n c_n phi_n stays in
+// its registers, phi_{n-2} is read from the buffer that receives phi_n (same
+// thread, same entry).  One cluster barrier per term orders the writes of
+// phi_n before any CTA reads them and all reads of phi_{n-1} before the buffer
+// is overwritten.  Control flow is uniform over the cluster: an inactive row
+// returns in every CTA before the first barrier, and every thread of every
+// CTA passes each barrier (the per-configuration work is predicated).
+constexpr int kClusterMaxBits = 3;      // portable cluster sizes (<= 8 CTAs)
+constexpr int kClusterMaxLocal = 3520;  // 2 buffers x 4 planes x 8 B x Zl <= 225,280 B
+
+template <int KPT>
+struct ClusterCfg {
+  static constexpr int kNT = KPT <= 2 ? 1024 : 896;  // largest block of the instance
+};
+
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+
+// Barrier over every thread of the cluster; release/acquire order the
+// shared-memory writes of one term before the reads of the next.
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
+}
+
+// Complex value at shared-memory byte address `a` of the CTA `rank` of this cluster.
+__device__ __forceinline__ Cx<float> ld_peer(unsigned a, unsigned rank) {
+  unsigned ra;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+  Cx<float> v;
+  asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.re), "=f"(v.im) : "r"(ra));
+  return v;
+}
+
+__device__ __forceinline__ Cx<float> ld_plane(const float2* b, unsigned i) {
+  const float2 v = b[i];
+  return {v.x, v.y};
+}
+
+// Flip-flop of an isotropic nucleus on the electron of radical rr with the
+// partner that has the nuclear quantum number one lower ("up": S_- I_+ brings
+// it to this configuration) or one higher ("down"): g (u0, u1) is added to the
+// two electron components it reaches.  Components read from the partner:
+//   rr = 0: up (0, 1) -> y2, y3;  down (2, 3) -> y0, y1
+//   rr = 1: up (0, 2) -> y1, y3;  down (1, 3) -> y0, y2
+__device__ __forceinline__ void flip_add(Cx<float> (&y)[4], int rr, bool up, float g,
+                                         const Cx<float>& u0, const Cx<float>& u1) {
+  if (rr == 0) {
+    if (up) {
+      rmac(y[2], g, u0);
+      rmac(y[3], g, u1);
+    } else {
+      rmac(y[0], g, u0);
+      rmac(y[1], g, u1);
+    }
+  } else {
+    if (up) {
+      rmac(y[1], g, u0);
+      rmac(y[3], g, u1);
+    } else {
+      rmac(y[0], g, u0);
+      rmac(y[2], g, u1);
+    }
+  }
+}
+
+// Plane indices of the two components a flip-flop reads (see flip_add).
+__device__ __forceinline__ int flip_e0(int rr, bool up) { return rr == 0 ? (up ? 0 : 2) : (up ? 0 : 1); }
+__device__ __forceinline__ int flip_e1(int rr, bool up) { return rr == 0 ? (up ? 1 : 3) : (up ? 2 : 3); }
+
+template <int KPT>
+__global__ void __launch_bounds__(ClusterCfg<KPT>::kNT, 1) k_macro_cluster(
+    const HamDev<float> H, const FieldDev<float>* __restrict__ fields,
+    const int* __restrict__ row_field, const int2* __restrict__ row_win, int macro_arg,
+    const int* __restrict__ macro_dev, const float* __restrict__ P, float* __restrict__ Q,
+    float* __restrict__ X, const float* __restrict__ coef, int n_c, long long Zslot, int cbits,
+    int xblk) {
+  extern __shared__ __align__(16) float2 cl_smem[];
+  const int r = blockIdx.y;
+  {
+    const int macro = macro_dev ? *macro_dev : macro_arg;
+    const int2 w = row_win[r];
+    if (macro < w.x || macro >= w.y) return;  // the whole cluster: one row
+  }
+  const unsigned rank = cluster_rank();
+  const unsigned Zl = (unsigned)(H.Z >> cbits);
+  const int lb = H.n_half - cbits;
+  const unsigned lmask = (1u << lb) - 1u;
+  const unsigned NT = blockDim.x;
+  const int f = row_field[r];
+  const FieldDev<float> F = fields[f];
+  const float* cf = coef + (size_t)f * n_c * 2;
+  const size_t row0 = (size_t)r * Zslot * 8;
+  float* xr = X + (size_t)r * n_c * Zslot * 2;
+  const float s2 = 1.41421356237309504880f;
+
+  // psi(t) of the row into buffer 0 (plane e holds component e)
+#pragma unroll
+  for (int j = 0; j < KPT; ++j) {
+    const unsigned l = threadIdx.x + j * NT;
+    if (l < Zl) {
+      const unsigned m = ((l >> lb) << (lb + cbits)) | (rank << lb) | (l & lmask);
+      Cx<float> a[4];
+      load4(P + row0 + (size_t)m * 8, a);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) cl_smem[e * Zl + l] = make_float2(a[e].re, a[e].im);
+    }
+  }
+  Cx<float> acc[KPT][4];
+#pragma unroll
+  for (int j = 0; j < KPT; ++j)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc[j][e] = {0.f, 0.f};
+  cluster_barrier();
+
+  for (int n = 1; n < n_c; ++n) {
+    const float2* cur = cl_smem + ((n - 1) & 1) * 4 * Zl;  // phi_{n-1}
+    float2* oth = cl_smem + (n & 1) * 4 * Zl;              // phi_{n-2}, then phi_n
+    const unsigned cur_s = smem_u32(cur);
+    const float cr = cf[2 * n], ci = cf[2 * n + 1];
+#pragma unroll
+    for (int j = 0; j < KPT; ++j) {
+      const unsigned l = threadIdx.x + j * NT;
+      if (l >= Zl) continue;
+      Cx<float> a[4], y[4], z[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        a[e] = ld_plane(cur + e * Zl, l);
+        y[e] = {0.f, 0.f};
+      }
+      float b1[3] = {0.f, 0.f, 0.f}, b2[3] = {0.f, 0.f, 0.f};
+      // spin-1/2 nuclei inside the CTA: both directions weighted by the digit
+      // (not unrolled: fewer registers live next to the accumulators)
+#pragma unroll 1
+      for (int p = 0; p < lb; ++p) {
+        {
+          const unsigned jb = (l >> p) & 1u;
+          const unsigned lp = l ^ (1u << p);
+          const int rr = H.rad[p];
+          const float g = H.U[p][4];  // a/2
+          const float gu = jb ? 0.f : g, gd = jb ? g : 0.f;
+          if (rr == 0) {
+            const Cx<float> q0 = ld_plane(cur + (2 * jb) * Zl, lp);
+            const Cx<float> q1 = ld_plane(cur + (2 * jb + 1) * Zl, lp);
+            rmac(y[2], gu, q0);
+            rmac(y[3], gu, q1);
+            rmac(y[0], gd, q0);
+            rmac(y[1], gd, q1);
+            b1[2] += jb ? -g : g;
+          } else {
+            const Cx<float> q0 = ld_plane(cur + jb * Zl, lp);
+            const Cx<float> q1 = ld_plane(cur + (2 + jb) * Zl, lp);
+            rmac(y[1], gu, q0);
+            rmac(y[3], gu, q1);
+            rmac(y[0], gd, q0);
+            rmac(y[2], gd, q1);
+            b2[2] += jb ? -g : g;
+          }
+        }
+      }
+      // spin-1/2 nuclei that select the CTA: the partner is in CTA rank XOR 2^i,
+      // and the direction is the same for the whole CTA
+#pragma unroll
+      for (int i = 0; i < kClusterMaxBits; ++i) {
+        if (i < cbits) {
+          const int p = lb + i;
+          const bool up = ((rank >> i) & 1u) == 0u;
+          const unsigned peer = rank ^ (1u << i);
+          const int rr = H.rad[p];
+          const float g = H.U[p][4];
+          const Cx<float> u0 = ld_peer(cur_s + (flip_e0(rr, up) * Zl + l) * 8u, peer);
+          const Cx<float> u1 = ld_peer(cur_s + (flip_e1(rr, up) * Zl + l) * 8u, peer);
+          flip_add(y, rr, up, g, u0, u1);
+          if (rr == 0) b1[2] += up ? g : -g;
+          else b2[2] += up ? g : -g;
+        }
+      }
+      // spin-1 nuclei: base-3 digits of l >> lb (the same digits as m >> n_half)
+      unsigned qd = l >> lb;
+#pragma unroll 4
+      for (int p = H.n_half; p < H.n_half + H.n_one; ++p) {
+        const unsigned jd = qd % 3u;
+        qd /= 3u;
+        const int rr = H.rad[p];
+        const unsigned st = (unsigned)(H.stride[p] >> cbits);
+        const float g = s2 * H.U[p][4];
+        const float dz = (1.f - (float)jd) * H.v[p][2];
+        if (rr == 0) b1[2] += dz;
+        else b2[2] += dz;
+        if (jd < 2u) {
+          const unsigned lp = l + st;
+          flip_add(y, rr, true, g, ld_plane(cur + flip_e0(rr, true) * Zl, lp),
+                   ld_plane(cur + flip_e1(rr, true) * Zl, lp));
+        }
+        if (jd > 0u) {
+          const unsigned lp = l - st;
+          flip_add(y, rr, false, g, ld_plane(cur + flip_e0(rr, false) * Zl, lp),
+                   ld_plane(cur + flip_e1(rr, false) * Zl, lp));
+        }
+      }
+      // any higher spin
+      for (int p = H.n_half + H.n_one; p < H.n_nuc; ++p) {
+        const unsigned d = (unsigned)H.d[p];
+        const unsigned jd = qd % d;
+        qd /= d;
+        const int rr = H.rad[p];
+        const unsigned st = (unsigned)(H.stride[p] >> cbits);
+        const float I = 0.5f * (float)(d - 1), M = I - (float)jd;
+        const float dz = M * H.v[p][2];
+        if (rr == 0) b1[2] += dz;
+        else b2[2] += dz;
+        if (jd + 1u < d) {
+          const unsigned lp = l + st;
+          flip_add(y, rr, true, sqrtf(I * (I + 1.f) - M * (M - 1.f)) * H.U[p][4],
+                   ld_plane(cur + flip_e0(rr, true) * Zl, lp),
+                   ld_plane(cur + flip_e1(rr, true) * Zl, lp));
+        }
+        if (jd > 0u) {
+          const unsigned lp = l - st;
+          flip_add(y, rr, false, sqrtf(I * (I + 1.f) - M * (M + 1.f)) * H.U[p][4],
+                   ld_plane(cur + flip_e0(rr, false) * Zl, lp),
+                   ld_plane(cur + flip_e1(rr, false) * Zl, lp));
+        }
+      }
+      finish_z<float, false>(H, F, a, y, b1, b2, z);
+      const unsigned m = ((l >> lb) << (lb + cbits)) | (rank << lb) | (l & lmask);
+      Cx<float> ph[4];
+      if (n == 1) {
+        const float c0r = cf[0], c0i = cf[1];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          ph[e] = z[e];
+          cmac(acc[j][e], c0r, c0i, a[e]);
+        }
+        if (xblk) store_singlet_blk(xblk_addr(X, r, 0, m, Zslot, n_c), a);
+        else store_singlet(xr + (size_t)m * 2, a);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const Cx<float> pv = ld_plane(oth + e * Zl, l);
+          ph[e].re = 2.f * z[e].re - pv.re;
+          ph[e].im = 2.f * z[e].im - pv.im;
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) cmac(acc[j][e], cr, ci, ph[e]);
+      if (n < n_c - 1) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) oth[e * Zl + l] = make_float2(ph[e].re, ph[e].im);
+      }
+      if (xblk) store_singlet_blk(xblk_addr(X, r, n, m, Zslot, n_c), ph);
+      else store_singlet(xr + ((size_t)n * Zslot + m) * 2, ph);
+    }
+    cluster_barrier();
+  }
+  // psi(t + h) = the accumulator (no peer reads after the last barrier)
+#pragma unroll
+  for (int j = 0; j < KPT; ++j) {
+    const unsigned l = threadIdx.x + j * NT;
+    if (l < Zl) {
+      const unsigned m = ((l >> lb) << (lb + cbits)) | (rank << lb) | (l & lmask);
+      store4(Q + row0 + (size_t)m * 8, acc[j]);
+    }
+  }
+}
+
 // Exact time integral of one macro-step (Eq. 20 / Eq. 22 over [t, t + h]):
 //   integral[r] += sum_nm W_nm G_nm,  G_nm = sum_z conj(x_n(z)) x_m(z),
 // where x_n = <S|phi_n> are the singlet slices stored by the step kernel.
@@ -1406,6 +1690,108 @@ cudaError_t launch_macro_small(const SysTab<T>& S, const HamDev<T>* one, int ani
   }
 #undef RP_LAUNCH_SMALL
   return cudaGetLastError();
+}
+
+bool macro_cluster_plan(const HamDev<float>& H, ClusterPlan* out) {
+  if (H.aniso || H.Z < 1) return false;
+  int c = -1;
+  for (int b = 0; b <= kClusterMaxBits && b <= H.n_half; ++b)
+    if ((H.Z >> b) <= kClusterMaxLocal) {
+      c = b;
+      break;
+    }
+  if (c < 0) return false;
+  ClusterPlan P;
+  P.cbits = c;
+  P.local = (int)(H.Z >> c);
+  P.kpt = P.local <= 1024 ? 1 : P.local <= 2048 ? 2 : P.local <= 2688 ? 3 : 4;
+  P.threads = ((P.local + P.kpt - 1) / P.kpt + 31) / 32 * 32;
+  P.smem = (size_t)2 * 4 * P.local * sizeof(float2);
+  if (out) *out = P;
+  return true;
+}
+
+cudaError_t launch_macro_cluster(const HamDev<float>& H, const FieldDev<float>* fields,
+                                 const int* row_field, const int2* row_win, int macro,
+                                 const int* macro_dev, int rows, const float* P, float* Q,
+                                 float* X, const float* coef, int n_c, long long Zslot, int xblk,
+                                 cudaStream_t st) {
+  if (rows == 0) return cudaSuccess;
+  ClusterPlan cp;
+  if (!macro_cluster_plan(H, &cp)) return cudaErrorNotSupported;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(1u << cp.cbits, (unsigned)rows, 1);
+  cfg.blockDim = dim3((unsigned)cp.threads, 1, 1);
+  cfg.dynamicSmemBytes = cp.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 1u << cp.cbits;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  static std::atomic<unsigned long long> attr_done[4];
+  const int smax = 2 * 4 * kClusterMaxLocal * (int)sizeof(float2);
+#define RP_LAUNCH_CLUSTER(K)                                                                       \
+  {                                                                                                \
+    cudaError_t e = smem_attr_once((const void*)k_macro_cluster<K>, smax, attr_done[K - 1]);      \
+    if (e != cudaSuccess) return e;                                                                \
+    e = cudaLaunchKernelEx(&cfg, k_macro_cluster<K>, H, fields, row_field, row_win, macro,        \
+                           macro_dev, P, Q, X, coef, n_c, Zslot, cp.cbits, xblk);                  \
+    if (e != cudaSuccess) return e;                                                                \
+  }
+  switch (cp.kpt) {
+    case 1: RP_LAUNCH_CLUSTER(1) break;
+    case 2: RP_LAUNCH_CLUSTER(2) break;
+    case 3: RP_LAUNCH_CLUSTER(3) break;
+    default: RP_LAUNCH_CLUSTER(4) break;
+  }
+#undef RP_LAUNCH_CLUSTER
+  return cudaGetLastError();
+}
+
+int macro_cluster_max_active(const HamDev<float>& H) {
+  ClusterPlan cp;
+  if (!macro_cluster_plan(H, &cp)) return 0;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(1u << cp.cbits, 1, 1);
+  cfg.blockDim = dim3((unsigned)cp.threads, 1, 1);
+  cfg.dynamicSmemBytes = cp.smem;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 1u << cp.cbits;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  static std::atomic<unsigned long long> attr_done[4];
+  const int smax = 2 * 4 * kClusterMaxLocal * (int)sizeof(float2);
+  int n = 0;
+  cudaError_t e = cudaSuccess;
+  switch (cp.kpt) {
+    case 1:
+      e = smem_attr_once((const void*)k_macro_cluster<1>, smax, attr_done[0]);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n, k_macro_cluster<1>, &cfg);
+      break;
+    case 2:
+      e = smem_attr_once((const void*)k_macro_cluster<2>, smax, attr_done[1]);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n, k_macro_cluster<2>, &cfg);
+      break;
+    case 3:
+      e = smem_attr_once((const void*)k_macro_cluster<3>, smax, attr_done[2]);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n, k_macro_cluster<3>, &cfg);
+      break;
+    default:
+      e = smem_attr_once((const void*)k_macro_cluster<4>, smax, attr_done[3]);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n, k_macro_cluster<4>, &cfg);
+      break;
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
 }
 
 template <typename T>

@@ -131,6 +131,28 @@ cudaError_t launch_macro_small(const SysTab<T>& S, const HamDev<T>* one, int ani
                                const int2* row_win, int macro, const int* macro_dev, int rows,
                                const T* P, T* Q, T* X, const T* coef, int n_c, cudaStream_t st);
 
+// A whole macro-step of every active row of one isotropic FP32 system on a
+// thread-block cluster per row, the row's Chebyshev vectors in distributed
+// shared memory (see k_macro_cluster): reads psi from P, writes the propagated
+// psi to Q and the singlet slices to X (tensor-core layout if xblk).
+// macro_cluster_plan: whether the system fits (isotropic, Z / 2^c <= 3520 with
+// c <= min(3, n_half)), and the launch shape; macro_cluster_max_active:
+// clusters of that shape that fit the device at once (0 if none or on error).
+struct ClusterPlan {
+  int cbits = 0;    // log2 of the CTAs per cluster (per row)
+  int local = 0;    // configurations per CTA
+  int kpt = 1;      // configurations per thread
+  int threads = 0;  // threads per CTA
+  size_t smem = 0;  // dynamic shared memory per CTA
+};
+bool macro_cluster_plan(const HamDev<float>& H, ClusterPlan* out);
+int macro_cluster_max_active(const HamDev<float>& H);
+cudaError_t launch_macro_cluster(const HamDev<float>& H, const FieldDev<float>* fields,
+                                 const int* row_field, const int2* row_win, int macro,
+                                 const int* macro_dev, int rows, const float* P, float* Q,
+                                 float* X, const float* coef, int n_c, long long Zslot, int xblk,
+                                 cudaStream_t st);
+
 // integral[r] += sum_nm W_nm <x_n|x_m> for the macro-step just finished
 // (x_n = singlet slices X[r][n], W per field); one FP64 atomic per CTA.
 template <typename T>

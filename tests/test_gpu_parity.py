@@ -303,6 +303,59 @@ def test_kernel_paths_agree(prec):
         assert b["stats"]["step_launches"] < a["stats"]["step_launches"]
 
 
+# systems the cluster macro-step kernel splits over 1, 2, 4 and 8 CTAs
+# (isotropic; spin-1/2, spin-1 and spin-3/2 nuclei; J and k_S != k_T)
+CLUSTER = [
+    ("c1_spin32", lambda: wl.random_isotropic(5, 4, two_I=[1, 1, 1, 2, 3, 1, 1, 1, 2], k_S=1.0,
+                                              k_T=3.0, J=0.2, seed=50)),            # Z = 2304
+    ("c2_one_half", lambda: wl.random_isotropic(4, 4, two_I=[1, 2, 2, 2, 2, 2, 2, 2], k_S=0.5,
+                                                k_T=2.0, seed=51)),                 # Z = 4374
+    ("c4", lambda: wl.random_isotropic(6, 5, two_I=[1, 1, 1, 1, 2, 2, 1, 1, 1, 2, 2], k_S=2.0,
+                                       k_T=0.7, J=-0.3, seed=52)),                  # Z = 10368
+    ("c8_config2", lambda: wl.config2().system),                                    # Z = 20736
+]
+
+
+@pytest.mark.parametrize("name,mk", CLUSTER, ids=[c[0] for c in CLUSTER])
+def test_cluster_macro_step_matches_per_term_and_oracle(name, mk):
+    """The cluster macro-step kernel (kernel = 4: a row's Chebyshev vectors in
+    the distributed shared memory of 2^c CTAs) gives the per-term kernels'
+    per-sample yields at the FP32 tolerance, with the tensor-core and the
+    CUDA-core time integrals, and one row agrees with the FP64 oracle."""
+    rp = _rp()
+    s = mk()
+    sy = rp.System(s)
+    fields = np.array([0.0, 3.0, 12.0])
+    M, T = 3, 0.12
+    ref = sy.yields(fields, M, 5, T, per_sample=True, precision="fp32", kernel=1)
+    for gram in (2, 1):
+        got = sy.yields(fields, M, 5, T, per_sample=True, precision="fp32", kernel=4, gram=gram)
+        assert got["stats"]["step_launches"] < ref["stats"]["step_launches"], "cluster path not taken"
+        e = _cmp_per_sample(got["per_sample"].reshape(-1, 3), ref["per_sample"][..., 0].ravel(),
+                            ref["per_sample"][..., 1].ravel(), ref["per_sample"][..., 2].ravel(),
+                            "fp32")
+        assert e < 1e-5
+    psi0 = coherent.sample_states(s, 5, [2])
+    o = chebyshev.propagate_yields(s, fields[2], T, psi0[0])
+    g = got["per_sample"][2, 2]
+    assert abs(g[0] - o[0]) < TOL["fp32"] * abs(o[0])
+    assert abs(g[1] - o[1]) < TOL["fp32"] * max(abs(o[1]), abs(o[0]))
+    assert abs(g[2] - o[2]) < TOL["fp32"]
+
+
+def test_cluster_macro_step_graph_replay_and_refill():
+    """Cluster macro-steps replayed from CUDA graphs, with rows refilled
+    between macro-steps, equal the eager cluster launches."""
+    rp = _rp()
+    sy = rp.System(CLUSTER[2][1]())
+    fields = [0.0, 2.0, 6.0]
+    a = sy.yields(fields, 5, 3, 0.3, per_sample=True, precision="fp32", kernel=4, max_rows=4)
+    b = sy.yields(fields, 5, 3, 0.3, per_sample=True, precision="fp32", kernel=4, max_rows=4,
+                  graph=1)
+    assert np.allclose(a["per_sample"], b["per_sample"], rtol=1e-12, atol=1e-14)
+    assert b["stats"]["graph_launches"] > 0
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_graph_replay_matches_eager(prec):
     """Macro-steps replayed from CUDA graphs (kernels reading the macro-step
