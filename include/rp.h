@@ -84,7 +84,11 @@ typedef struct rp_options {
   uint32_t pair_id;       /* Philox counter word 3 (radical-pair id) */
   int profile;            /* 1: time the H.psi step kernels with CUDA events */
   void* stream;           /* cudaStream_t, NULL: the legacy default stream */
-  int kernel;             /* 0: choose; 1: one launch per Chebyshev term (any Z);
+  int kernel;             /* 0: choose (2 where Z fits one CTA's shared memory; 4
+                             for the FP32 shapes with a compiled cluster
+                             instance -- 8 spin-1/2 and 4 spin-1 nuclei,
+                             isotropic, one system; else 1);
+                             1: one launch per Chebyshev term (any Z);
                              2: a whole macro-step per launch with each row's
                              vectors in shared memory (Z <= 2048 FP32, 1024
                              FP64; larger Z falls back to 1); 3: as 1, and FP32

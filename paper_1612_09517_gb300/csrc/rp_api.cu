@@ -156,6 +156,22 @@ rp::LayoutDev make_layout(const rp::HostSystem& s) {
 
 int default_ncheb(int) { return 88; }  // fastest measured in both precisions (rp_tune)
 
+}  // namespace
+
+namespace rp {
+// Kernel path rp_yields takes for kernel = 0 on one FP32 system (rp_tune's
+// baseline), and whether the cluster path (kernel = 4) applies to it.
+int default_kernel_fp32(const HostSystem& hs, bool* cluster_ok) {
+  const HamDev<float> hf = make_ham<float>(hs);
+  const bool ok = macro_cluster_plan(hf, nullptr);
+  if (cluster_ok) *cluster_ok = ok;
+  if (hs.Z <= small_max_configs<float>()) return 2;
+  return macro_cluster_default(hf) ? 4 : 1;
+}
+}  // namespace rp
+
+namespace {
+
 bool bad_kernel_choice(const rp_options& o) {
   return o.kernel < 0 || o.kernel > 4 || o.graph < 0 || o.graph > 1 || o.gram < 0 || o.gram > 2;
 }
@@ -270,9 +286,11 @@ class YieldEngine {
     // a whole macro-step per launch on a thread-block cluster per row (FP32,
     // one isotropic system whose state fits the cluster's shared memory)
     cluster_ = false;
-    if (sizeof(T) == 4 && !small_ && sys_.size() == 1 && o_.kernel == 4) {
+    if (sizeof(T) == 4 && !small_ && sys_.size() == 1 && (o_.kernel == 4 || o_.kernel == 0)) {
       const auto& hf = *reinterpret_cast<const rp::HamDev<float>*>(&ham1_);
-      cluster_ = rp::macro_cluster_plan(hf, nullptr) && rp::macro_cluster_max_active(hf) > 0;
+      cluster_ = (o_.kernel == 4 ? rp::macro_cluster_plan(hf, nullptr)
+                                 : rp::macro_cluster_default(hf)) &&
+                 rp::macro_cluster_max_active(hf) > 0;
     }
     // tensor-core time integral: FP32 with the per-term kernels (each row's
     // integral covers its own system's Z; the step kernel keeps the padding of

@@ -909,34 +909,51 @@ __global__ void __launch_bounds__(256) k_macro_small(
 }
 
 // ---- whole macro-steps of mid-size systems on a thread-block cluster ----
-// For an isotropic FP32 system whose state splits over C = 2^c CTAs of one
-// cluster (c <= kClusterMaxBits) with Zl = Z / C <= kClusterMaxLocal
-// configurations per CTA, the cluster holds a row's phi_{n-1} and phi_n in
-// distributed shared memory for a whole macro-step: HBM sees psi in, psi out
-// and the singlet slices only.  The CTA rank is the value of the c outermost
-// spin-1/2 nuclei (layout positions lb .. n_half - 1, lb = n_half - c), so the
-// configuration m of local index l is
+// For an isotropic FP32 system of spin-1/2 and spin-1 nuclei whose state
+// splits over C = 2^c CTAs of one cluster (c <= kClusterMaxBits) with
+// Zl = Z / C <= kClusterMaxLocal configurations per CTA, the cluster holds a
+// row's phi_{n-1} and phi_n in distributed shared memory for a whole
+// macro-step: HBM sees psi in, psi out and the singlet slices only.  The CTA
+// rank is the value of the c outermost spin-1/2 nuclei (layout positions
+// lb .. n_half - 1, lb = n_half - c), so the configuration of local index l is
 //   m = ((l >> lb) << (lb + c)) | (rank << lb) | (l & (2^lb - 1)),
 // and the partners of H.psi (Eq. 1, isotropic flip-flops) are
-//   spin-1/2 at p < lb:       l XOR 2^p in this CTA,
-//   spin-1/2 at lb + i:       the same l in CTA rank XOR 2^i (ld.shared::cluster),
-//   higher spins (p >= n_half): l +- stride_p / C in this CTA.
-// Shared memory per buffer: four planes of Zl complex values, one per electron
-// state e, so a flip-flop partner (two of the four components) costs two
-// contiguous 8-byte reads per thread.  Each thread owns the KPT local
-// configurations l = tid + j NT; the accumulator psi(h) = sum_n c_n phi_n stays in
-// its registers, phi_{n-2} is read from the buffer that receives phi_n (same
-// thread, same entry).  One cluster barrier per term orders the writes of
-// phi_n before any CTA reads them and all reads of phi_{n-1} before the buffer
-// is overwritten.  Control flow is uniform over the cluster: an inactive row
-// returns in every CTA before the first barrier, and every thread of every
-// CTA passes each barrier (the per-configuration work is predicated).
+//   spin-1/2 at p < lb:  l XOR 2^p in this CTA,
+//   spin-1/2 at lb + i:  the same l in CTA rank XOR 2^i (ld.shared::cluster),
+//   spin-1 (p >= n_half): l +- stride_p / C in this CTA.
+// Shared memory: two buffers of four planes (one per electron state e, Zl
+// complex values each), so a flip-flop partner (two of the four components)
+// costs two contiguous 8-byte reads per thread; then the accumulators
+// psi(h) = sum_n c_n phi_n of every configuration but each thread's first,
+// whose accumulator stays in registers.  Each thread owns the KPT local
+// configurations l = tid + j NT; phi_{n-2} is read from the buffer that
+// receives phi_n (same thread, same entry).  One cluster barrier per term
+// orders the writes of phi_n before any CTA reads them and all reads of
+// phi_{n-1} before the buffer is overwritten.  Control flow is uniform over
+// the cluster: an inactive row returns in every CTA before the first barrier,
+// and every thread of every CTA passes each barrier (the per-configuration
+// work is predicated).
 constexpr int kClusterMaxBits = 3;      // portable cluster sizes (<= 8 CTAs)
-constexpr int kClusterMaxLocal = 3520;  // 2 buffers x 4 planes x 8 B x Zl <= 225,280 B
+constexpr int kClusterMaxLocal = 2688;  // 64 Zl + 32 (Zl - NT) bytes of shared memory
+constexpr int kClusterMaxIn = 12;       // inner spin-1/2 nuclei (2^12 > kClusterMaxLocal)
+constexpr int kClusterMaxOne = 8;       // spin-1 nuclei (3^8 > kClusterMaxLocal)
+
+// Per-system constants of the cluster kernel, by layout position (rad/us):
+// radical bit masks, flip-flop couplings a/2 (spin-1/2) and sqrt(2) a/2
+// (spin-1), the spin-1 diagonal a and the spin-1 local strides in bytes of a plane.
+struct ClusterConst {
+  int Zl, lb, cbits, n_one, NT;
+  unsigned rr_in, rr_out, rr_one;
+  float g_in[kClusterMaxIn];
+  float g_out[kClusterMaxBits];
+  float g_one[kClusterMaxOne];
+  float v_one[kClusterMaxOne];
+  unsigned st_one[kClusterMaxOne];
+};
 
 template <int KPT>
 struct ClusterCfg {
-  static constexpr int kNT = KPT <= 2 ? 1024 : 896;  // largest block of the instance
+  static constexpr int kNT = KPT == 1 ? 1024 : 896;
 };
 
 __device__ __forceinline__ unsigned cluster_rank() {
@@ -951,7 +968,17 @@ __device__ __forceinline__ void cluster_barrier() {
   asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
 }
 
-// Complex value at shared-memory byte address `a` of the CTA `rank` of this cluster.
+// Complex values in shared memory (float2 = re, im).  Plain loads and stores,
+// so the compiler keeps them ordered against the cluster barrier (its memory
+// clobber) and schedules them freely between barriers; a peer CTA's shared
+// memory is reached through a generic pointer from __cluster_map_shared_rank.
+__device__ __forceinline__ Cx<float> ldc(const float2* p) {
+  const float2 v = *p;
+  return {v.x, v.y};
+}
+__device__ __forceinline__ void stc(float2* p, const Cx<float>& v) { *p = make_float2(v.re, v.im); }
+// Complex value at shared-memory byte address a of the CTA `rank` of this
+// cluster (volatile: it stays between the cluster barriers around it).
 __device__ __forceinline__ Cx<float> ld_peer(unsigned a, unsigned rank) {
   unsigned ra;
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
@@ -960,49 +987,50 @@ __device__ __forceinline__ Cx<float> ld_peer(unsigned a, unsigned rank) {
   return v;
 }
 
-__device__ __forceinline__ Cx<float> ld_plane(const float2* b, unsigned i) {
-  const float2 v = b[i];
-  return {v.x, v.y};
-}
-
 // Flip-flop of an isotropic nucleus on the electron of radical rr with the
-// partner that has the nuclear quantum number one lower ("up": S_- I_+ brings
-// it to this configuration) or one higher ("down"): g (u0, u1) is added to the
-// two electron components it reaches.  Components read from the partner:
+// partner whose nuclear quantum number is one lower ("up": S_- I_+ brings it
+// to this configuration) or one higher ("down"); g (u0, u1) goes to the two
+// electron components it reaches.  Components read from the partner:
 //   rr = 0: up (0, 1) -> y2, y3;  down (2, 3) -> y0, y1
 //   rr = 1: up (0, 2) -> y1, y3;  down (1, 3) -> y0, y2
-__device__ __forceinline__ void flip_add(Cx<float> (&y)[4], int rr, bool up, float g,
+template <bool UP>
+__device__ __forceinline__ void flip_add(Cx<float> (&y)[4], unsigned rr, float g,
                                          const Cx<float>& u0, const Cx<float>& u1) {
-  if (rr == 0) {
-    if (up) {
-      rmac(y[2], g, u0);
-      rmac(y[3], g, u1);
-    } else {
-      rmac(y[0], g, u0);
-      rmac(y[1], g, u1);
-    }
+  if (rr == 0u) {
+    rmac(y[UP ? 2 : 0], g, u0);
+    rmac(y[UP ? 3 : 1], g, u1);
   } else {
-    if (up) {
-      rmac(y[1], g, u0);
-      rmac(y[3], g, u1);
-    } else {
-      rmac(y[0], g, u0);
-      rmac(y[2], g, u1);
-    }
+    rmac(y[UP ? 1 : 0], g, u0);
+    rmac(y[UP ? 3 : 2], g, u1);
   }
 }
 
-// Plane indices of the two components a flip-flop reads (see flip_add).
-__device__ __forceinline__ int flip_e0(int rr, bool up) { return rr == 0 ? (up ? 0 : 2) : (up ? 0 : 1); }
-__device__ __forceinline__ int flip_e1(int rr, bool up) { return rr == 0 ? (up ? 1 : 3) : (up ? 2 : 3); }
+// Byte offsets (in units of one plane) of the two partner components read by
+// a flip-flop (see flip_add).
+template <bool UP>
+__device__ __forceinline__ unsigned flip_p0(unsigned rr) { return UP ? 0u : (rr == 0u ? 2u : 1u); }
+template <bool UP>
+__device__ __forceinline__ unsigned flip_p1(unsigned rr) { return UP ? (rr == 0u ? 1u : 2u) : 3u; }
 
-template <int KPT>
+// Shape of a cluster instance: LB inner spin-1/2 nuclei, CB = log2 of the
+// CTAs, N1 spin-1 nuclei, all known at compile time (LB >= 0), or read from
+// ClusterConst (LB = -1: any shape the plan accepts).
+template <int LB, int N1>
+struct ClusterShape {
+  static constexpr bool kStatic = LB >= 0;
+  static constexpr int kIn = kStatic ? LB : kClusterMaxIn;     // unrolled inner nuclei
+  static constexpr int kOne = kStatic ? N1 : kClusterMaxOne;   // unrolled spin-1 nuclei
+  __host__ __device__ static constexpr int pow3(int n) { return n == 0 ? 1 : 3 * pow3(n - 1); }
+  static constexpr unsigned kZl = kStatic ? (1u << (LB < 0 ? 0 : LB)) * pow3(N1 < 0 ? 0 : N1) : 0u;
+};
+
+template <int LB, int CB, int N1, int KPT>
 __global__ void __launch_bounds__(ClusterCfg<KPT>::kNT, 1) k_macro_cluster(
-    const HamDev<float> H, const FieldDev<float>* __restrict__ fields,
+    const ClusterConst K, const HamDev<float> H, const FieldDev<float>* __restrict__ fields,
     const int* __restrict__ row_field, const int2* __restrict__ row_win, int macro_arg,
     const int* __restrict__ macro_dev, const float* __restrict__ P, float* __restrict__ Q,
-    float* __restrict__ X, const float* __restrict__ coef, int n_c, long long Zslot, int cbits,
-    int xblk) {
+    float* __restrict__ X, const float* __restrict__ coef, int n_c, long long Zslot, int xblk) {
+  using Sh = ClusterShape<LB, N1>;
   extern __shared__ __align__(16) float2 cl_smem[];
   const int r = blockIdx.y;
   {
@@ -1011,183 +1039,211 @@ __global__ void __launch_bounds__(ClusterCfg<KPT>::kNT, 1) k_macro_cluster(
     if (macro < w.x || macro >= w.y) return;  // the whole cluster: one row
   }
   const unsigned rank = cluster_rank();
-  const unsigned Zl = (unsigned)(H.Z >> cbits);
-  const int lb = H.n_half - cbits;
+  const unsigned Zl = Sh::kStatic ? Sh::kZl : (unsigned)K.Zl;
+  const unsigned NT = (unsigned)K.NT;
+  const int lb = Sh::kStatic ? LB : K.lb;
+  const int cbits = Sh::kStatic ? CB : K.cbits;
+  const int n_one = Sh::kStatic ? N1 : K.n_one;
   const unsigned lmask = (1u << lb) - 1u;
-  const unsigned NT = blockDim.x;
+  // buffer b, plane e: cl_smem + (4 b + e) Zl; accumulators of l >= NT after
+  // the two buffers, plane e at + e (Zl - NT)
+  const unsigned apl = Zl > NT ? Zl - NT : 0u;
+  float2* accs = cl_smem + 8u * Zl - NT;
+  const unsigned sbase = smem_u32(cl_smem);
   const int f = row_field[r];
   const FieldDev<float> F = fields[f];
   const float* cf = coef + (size_t)f * n_c * 2;
-  const size_t row0 = (size_t)r * Zslot * 8;
-  float* xr = X + (size_t)r * n_c * Zslot * 2;
-  const float s2 = 1.41421356237309504880f;
+  const float* Pr = P + (size_t)r * Zslot * 8;
+  float* Qr = Q + (size_t)r * Zslot * 8;
+  float* Xr = xblk ? X + (size_t)r * xblk_row_floats(Zslot, n_c) : X + (size_t)r * n_c * Zslot * 2;
+  const unsigned tid = threadIdx.x;
 
-  // psi(t) of the row into buffer 0 (plane e holds component e)
+  // configuration index and singlet-slice offset of each owned configuration
+  unsigned mj[KPT], xj[KPT];
 #pragma unroll
   for (int j = 0; j < KPT; ++j) {
-    const unsigned l = threadIdx.x + j * NT;
-    if (l < Zl) {
-      const unsigned m = ((l >> lb) << (lb + cbits)) | (rank << lb) | (l & lmask);
-      Cx<float> a[4];
-      load4(P + row0 + (size_t)m * 8, a);
+    const unsigned l = tid + j * NT;
+    const unsigned m = ((l >> lb) << (lb + cbits)) | (rank << lb) | (l & lmask);
+    mj[j] = m;
+    xj[j] = xblk ? (m / kXChunk) * xrows_pad(n_c) * kXChunk + ((m % kXChunk) >> 2) * 32 + (m & 3)
+                 : 2 * m;
+  }
+  // psi(t) of the row into buffer 0
 #pragma unroll
-      for (int e = 0; e < 4; ++e) cl_smem[e * Zl + l] = make_float2(a[e].re, a[e].im);
+  for (int j = 0; j < KPT; ++j) {
+    const unsigned l = tid + j * NT;
+    if (l < Zl) {
+      Cx<float> a[4];
+      load4(Pr + (size_t)mj[j] * 8, a);
+#pragma unroll
+      for (int e = 0; e < 4; ++e) stc(cl_smem + e * Zl + l, a[e]);
     }
   }
-  Cx<float> acc[KPT][4];
-#pragma unroll
-  for (int j = 0; j < KPT; ++j)
-#pragma unroll
-    for (int e = 0; e < 4; ++e) acc[j][e] = {0.f, 0.f};
+  Cx<float> acc0[4];
   cluster_barrier();
 
   for (int n = 1; n < n_c; ++n) {
-    const float2* cur = cl_smem + ((n - 1) & 1) * 4 * Zl;  // phi_{n-1}
-    float2* oth = cl_smem + (n & 1) * 4 * Zl;              // phi_{n-2}, then phi_n
-    const unsigned cur_s = smem_u32(cur);
+    const unsigned bo = ((n - 1) & 1) * 4u * Zl;  // phi_{n-1} in buffer (n - 1) % 2
+    const float2* cur = cl_smem + bo;
+    float2* oth = cl_smem + (4u * Zl - bo);        // phi_{n-2}, then phi_n
     const float cr = cf[2 * n], ci = cf[2 * n + 1];
+    // offset of slice n in a chunk (tensor-core layout) or of X[n] (plain)
+    const unsigned xn = xblk ? ((2 * n) >> 3) * 128 + ((2 * n) & 7) * 4 : (unsigned)(2 * n * Zslot);
+    const unsigned ximag = xblk ? 4u : 1u;
 #pragma unroll
     for (int j = 0; j < KPT; ++j) {
-      const unsigned l = threadIdx.x + j * NT;
+      const unsigned l = tid + j * NT;
       if (l >= Zl) continue;
-      Cx<float> a[4], y[4], z[4];
+      Cx<float> a[4], y[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        a[e] = ld_plane(cur + e * Zl, l);
+        a[e] = ldc(cur + e * Zl + l);
         y[e] = {0.f, 0.f};
       }
-      float b1[3] = {0.f, 0.f, 0.f}, b2[3] = {0.f, 0.f, 0.f};
+      float bz1 = 0.f, bz2 = 0.f;
+      // spin-1/2 nuclei that select the CTA: partner in CTA rank XOR 2^i, the
+      // direction is the same for the whole CTA
+#pragma unroll
+      for (int i = 0; i < (Sh::kStatic ? CB : kClusterMaxBits); ++i) {
+        if (Sh::kStatic || i < cbits) {
+          const unsigned pc = sbase + (bo + l) * 8u, peer = rank ^ (1u << i);
+          const unsigned rr = (K.rr_out >> i) & 1u;
+          const float g = K.g_out[i];
+          if ((rank >> i) & 1u) {
+            flip_add<false>(y, rr, g, ld_peer(pc + flip_p0<false>(rr) * Zl * 8u, peer),
+                            ld_peer(pc + flip_p1<false>(rr) * Zl * 8u, peer));
+            if (rr == 0u) bz1 -= g;
+            else bz2 -= g;
+          } else {
+            flip_add<true>(y, rr, g, ld_peer(pc + flip_p0<true>(rr) * Zl * 8u, peer),
+                           ld_peer(pc + flip_p1<true>(rr) * Zl * 8u, peer));
+            if (rr == 0u) bz1 += g;
+            else bz2 += g;
+          }
+        }
+      }
       // spin-1/2 nuclei inside the CTA: both directions weighted by the digit
-      // (not unrolled: fewer registers live next to the accumulators)
-#pragma unroll 1
-      for (int p = 0; p < lb; ++p) {
-        {
+#pragma unroll
+      for (int p = 0; p < Sh::kIn; ++p) {
+        if (Sh::kStatic || p < lb) {
           const unsigned jb = (l >> p) & 1u;
-          const unsigned lp = l ^ (1u << p);
-          const int rr = H.rad[p];
-          const float g = H.U[p][4];  // a/2
+          const float2* q8 = cur + (l ^ (1u << p));
+          const unsigned rr = (K.rr_in >> p) & 1u;
+          const float g = K.g_in[p];
           const float gu = jb ? 0.f : g, gd = jb ? g : 0.f;
-          if (rr == 0) {
-            const Cx<float> q0 = ld_plane(cur + (2 * jb) * Zl, lp);
-            const Cx<float> q1 = ld_plane(cur + (2 * jb + 1) * Zl, lp);
+          const float dz = jb ? -g : g;
+          if (rr == 0u) {
+            const float2* q = q8 + jb * 2u * Zl;
+            const Cx<float> q0 = ldc(q);
+            const Cx<float> q1 = ldc(q + Zl);
             rmac(y[2], gu, q0);
             rmac(y[3], gu, q1);
             rmac(y[0], gd, q0);
             rmac(y[1], gd, q1);
-            b1[2] += jb ? -g : g;
+            bz1 += dz;
           } else {
-            const Cx<float> q0 = ld_plane(cur + jb * Zl, lp);
-            const Cx<float> q1 = ld_plane(cur + (2 + jb) * Zl, lp);
+            const float2* q = q8 + jb * Zl;
+            const Cx<float> q0 = ldc(q);
+            const Cx<float> q1 = ldc(q + 2u * Zl);
             rmac(y[1], gu, q0);
             rmac(y[3], gu, q1);
             rmac(y[0], gd, q0);
             rmac(y[2], gd, q1);
-            b2[2] += jb ? -g : g;
+            bz2 += dz;
           }
         }
       }
-      // spin-1/2 nuclei that select the CTA: the partner is in CTA rank XOR 2^i,
-      // and the direction is the same for the whole CTA
-#pragma unroll
-      for (int i = 0; i < kClusterMaxBits; ++i) {
-        if (i < cbits) {
-          const int p = lb + i;
-          const bool up = ((rank >> i) & 1u) == 0u;
-          const unsigned peer = rank ^ (1u << i);
-          const int rr = H.rad[p];
-          const float g = H.U[p][4];
-          const Cx<float> u0 = ld_peer(cur_s + (flip_e0(rr, up) * Zl + l) * 8u, peer);
-          const Cx<float> u1 = ld_peer(cur_s + (flip_e1(rr, up) * Zl + l) * 8u, peer);
-          flip_add(y, rr, up, g, u0, u1);
-          if (rr == 0) b1[2] += up ? g : -g;
-          else b2[2] += up ? g : -g;
-        }
-      }
-      // spin-1 nuclei: base-3 digits of l >> lb (the same digits as m >> n_half)
+      // spin-1 nuclei: base-3 digits of l >> lb (the digits of m >> n_half)
       unsigned qd = l >> lb;
-#pragma unroll 4
-      for (int p = H.n_half; p < H.n_half + H.n_one; ++p) {
-        const unsigned jd = qd % 3u;
-        qd /= 3u;
-        const int rr = H.rad[p];
-        const unsigned st = (unsigned)(H.stride[p] >> cbits);
-        const float g = s2 * H.U[p][4];
-        const float dz = (1.f - (float)jd) * H.v[p][2];
-        if (rr == 0) b1[2] += dz;
-        else b2[2] += dz;
-        if (jd < 2u) {
-          const unsigned lp = l + st;
-          flip_add(y, rr, true, g, ld_plane(cur + flip_e0(rr, true) * Zl, lp),
-                   ld_plane(cur + flip_e1(rr, true) * Zl, lp));
-        }
-        if (jd > 0u) {
-          const unsigned lp = l - st;
-          flip_add(y, rr, false, g, ld_plane(cur + flip_e0(rr, false) * Zl, lp),
-                   ld_plane(cur + flip_e1(rr, false) * Zl, lp));
-        }
-      }
-      // any higher spin
-      for (int p = H.n_half + H.n_one; p < H.n_nuc; ++p) {
-        const unsigned d = (unsigned)H.d[p];
-        const unsigned jd = qd % d;
-        qd /= d;
-        const int rr = H.rad[p];
-        const unsigned st = (unsigned)(H.stride[p] >> cbits);
-        const float I = 0.5f * (float)(d - 1), M = I - (float)jd;
-        const float dz = M * H.v[p][2];
-        if (rr == 0) b1[2] += dz;
-        else b2[2] += dz;
-        if (jd + 1u < d) {
-          const unsigned lp = l + st;
-          flip_add(y, rr, true, sqrtf(I * (I + 1.f) - M * (M - 1.f)) * H.U[p][4],
-                   ld_plane(cur + flip_e0(rr, true) * Zl, lp),
-                   ld_plane(cur + flip_e1(rr, true) * Zl, lp));
-        }
-        if (jd > 0u) {
-          const unsigned lp = l - st;
-          flip_add(y, rr, false, sqrtf(I * (I + 1.f) - M * (M + 1.f)) * H.U[p][4],
-                   ld_plane(cur + flip_e0(rr, false) * Zl, lp),
-                   ld_plane(cur + flip_e1(rr, false) * Zl, lp));
+#pragma unroll
+      for (int i = 0; i < Sh::kOne; ++i) {
+        if (Sh::kStatic || i < n_one) {
+          const unsigned jd = qd % 3u;
+          qd /= 3u;
+          const unsigned rr = (K.rr_one >> i) & 1u;
+          const float g = K.g_one[i];
+          const float dz = (1.f - (float)jd) * K.v_one[i];
+          if (rr == 0u) bz1 += dz;
+          else bz2 += dz;
+          const unsigned st = Sh::kStatic ? (1u << LB) * ClusterShape<LB, N1>::pow3(i)
+                                          : K.st_one[i] / 8u;
+          if (jd < 2u) {
+            const float2* q = cur + l + st;
+            flip_add<true>(y, rr, g, ldc(q + flip_p0<true>(rr) * Zl), ldc(q + flip_p1<true>(rr) * Zl));
+          }
+          if (jd > 0u) {
+            const float2* q = cur + l - st;
+            flip_add<false>(y, rr, g, ldc(q + flip_p0<false>(rr) * Zl),
+                            ldc(q + flip_p1<false>(rr) * Zl));
+          }
         }
       }
+      const float b1[3] = {0.f, 0.f, bz1}, b2[3] = {0.f, 0.f, bz2};
+      Cx<float> z[4];
       finish_z<float, false>(H, F, a, y, b1, b2, z);
-      const unsigned m = ((l >> lb) << (lb + cbits)) | (rank << lb) | (l & lmask);
-      Cx<float> ph[4];
+      Cx<float> ph[4], s[4];
+      float2* al = accs + l;  // accumulator of l >= NT, plane e at + e apl
       if (n == 1) {
         const float c0r = cf[0], c0i = cf[1];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           ph[e] = z[e];
-          cmac(acc[j][e], c0r, c0i, a[e]);
+          s[e] = {0.f, 0.f};
+          cmac(s[e], c0r, c0i, a[e]);
         }
-        if (xblk) store_singlet_blk(xblk_addr(X, r, 0, m, Zslot, n_c), a);
-        else store_singlet(xr + (size_t)m * 2, a);
+        float* x0 = Xr + xj[j];
+        const float rs = 0.70710678118654752440f;
+        x0[0] = (a[1].re - a[2].re) * rs;
+        x0[ximag] = (a[1].im - a[2].im) * rs;
       } else {
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const Cx<float> pv = ld_plane(oth + e * Zl, l);
+          const Cx<float> pv = ldc(oth + e * Zl + l);
           ph[e].re = 2.f * z[e].re - pv.re;
           ph[e].im = 2.f * z[e].im - pv.im;
         }
+        if (j == 0) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) s[e] = acc0[e];
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) s[e] = ldc(al + e * apl);
+        }
       }
 #pragma unroll
-      for (int e = 0; e < 4; ++e) cmac(acc[j][e], cr, ci, ph[e]);
+      for (int e = 0; e < 4; ++e) cmac(s[e], cr, ci, ph[e]);
+      if (j == 0) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) acc0[e] = s[e];
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) stc(al + e * apl, s[e]);
+      }
       if (n < n_c - 1) {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) oth[e * Zl + l] = make_float2(ph[e].re, ph[e].im);
+        for (int e = 0; e < 4; ++e) stc(oth + e * Zl + l, ph[e]);
       }
-      if (xblk) store_singlet_blk(xblk_addr(X, r, n, m, Zslot, n_c), ph);
-      else store_singlet(xr + ((size_t)n * Zslot + m) * 2, ph);
+      float* xo = Xr + xj[j] + xn;
+      const float rs = 0.70710678118654752440f;
+      xo[0] = (ph[1].re - ph[2].re) * rs;
+      xo[ximag] = (ph[1].im - ph[2].im) * rs;
     }
     cluster_barrier();
   }
   // psi(t + h) = the accumulator (no peer reads after the last barrier)
 #pragma unroll
   for (int j = 0; j < KPT; ++j) {
-    const unsigned l = threadIdx.x + j * NT;
+    const unsigned l = tid + j * NT;
     if (l < Zl) {
-      const unsigned m = ((l >> lb) << (lb + cbits)) | (rank << lb) | (l & lmask);
-      store4(Q + row0 + (size_t)m * 8, acc[j]);
+      Cx<float> s[4];
+      if (j == 0) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) s[e] = acc0[e];
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) s[e] = ldc(accs + l + e * apl);
+      }
+      store4(Qr + (size_t)mj[j] * 8, s);
     }
   }
 }
@@ -1693,23 +1749,87 @@ cudaError_t launch_macro_small(const SysTab<T>& S, const HamDev<T>* one, int ani
 }
 
 bool macro_cluster_plan(const HamDev<float>& H, ClusterPlan* out) {
-  if (H.aniso || H.Z < 1) return false;
+  if (H.aniso || H.Z < 1 || H.n_half + H.n_one != H.n_nuc || H.n_one > kClusterMaxOne) return false;
   int c = -1;
   for (int b = 0; b <= kClusterMaxBits && b <= H.n_half; ++b)
     if ((H.Z >> b) <= kClusterMaxLocal) {
       c = b;
       break;
     }
-  if (c < 0) return false;
+  if (c < 0 || H.n_half - c > kClusterMaxIn) return false;
   ClusterPlan P;
   P.cbits = c;
   P.local = (int)(H.Z >> c);
-  P.kpt = P.local <= 1024 ? 1 : P.local <= 2048 ? 2 : P.local <= 2688 ? 3 : 4;
+  P.kpt = P.local <= 1024 ? 1 : (P.local <= 1792 ? 2 : 3);
   P.threads = ((P.local + P.kpt - 1) / P.kpt + 31) / 32 * 32;
-  P.smem = (size_t)2 * 4 * P.local * sizeof(float2);
+  P.smem = (size_t)64 * P.local + (size_t)32 * (P.local > P.threads ? P.local - P.threads : 0);
   if (out) *out = P;
   return true;
 }
+
+namespace {
+
+ClusterConst cluster_const(const HamDev<float>& H, const ClusterPlan& cp) {
+  ClusterConst K;
+  std::memset(&K, 0, sizeof(K));
+  K.Zl = cp.local;
+  K.cbits = cp.cbits;
+  K.lb = H.n_half - cp.cbits;
+  K.n_one = H.n_one;
+  K.NT = cp.threads;
+  for (int p = 0; p < H.n_nuc; ++p) {
+    const unsigned rr = H.rad[p] ? 1u : 0u;
+    if (p < K.lb) {
+      K.rr_in |= rr << p;
+      K.g_in[p] = H.U[p][4];
+    } else if (p < H.n_half) {
+      const int i = p - K.lb;
+      K.rr_out |= rr << i;
+      K.g_out[i] = H.U[p][4];
+    } else {
+      const int i = p - H.n_half;
+      K.rr_one |= rr << i;
+      K.g_one[i] = 1.41421356237309504880f * H.U[p][4];
+      K.v_one[i] = H.v[p][2];
+      K.st_one[i] = (unsigned)((H.stride[p] >> cp.cbits) * 8);
+    }
+  }
+  return K;
+}
+
+template <int LB, int CB, int N1, int KPT>
+cudaError_t cluster_attr(std::atomic<unsigned long long>& done) {
+  // the largest dynamic shared memory any launch of this instance asks for
+  return smem_attr_once((const void*)k_macro_cluster<LB, CB, N1, KPT>, 232448 - 1024, done);
+}
+
+std::atomic<unsigned long long> g_cluster_attr[4];
+
+cudaLaunchConfig_t cluster_cfg(const ClusterPlan& cp, int rows, cudaStream_t st,
+                               cudaLaunchAttribute* at) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(1u << cp.cbits, (unsigned)rows, 1);
+  cfg.blockDim = dim3((unsigned)cp.threads, 1, 1);
+  cfg.dynamicSmemBytes = cp.smem;
+  cfg.stream = st;
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 1u << cp.cbits;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+// Instance of a plan: 3 for the compiled shape (5 inner spin-1/2 nuclei, 8
+// CTAs, 4 spin-1 nuclei: the 12-nucleus workload with Z = 20736), else the
+// generic instance of its configurations per thread (0, 1, 2).
+int cluster_instance(const ClusterPlan& cp, const HamDev<float>& H) {
+  if (H.n_half - cp.cbits == 5 && cp.cbits == 3 && H.n_one == 4 && cp.kpt == 3) return 3;
+  return cp.kpt - 1;
+}
+
+}  // namespace
 
 cudaError_t launch_macro_cluster(const HamDev<float>& H, const FieldDev<float>* fields,
                                  const int* row_field, const int2* row_win, int macro,
@@ -1719,74 +1839,48 @@ cudaError_t launch_macro_cluster(const HamDev<float>& H, const FieldDev<float>* 
   if (rows == 0) return cudaSuccess;
   ClusterPlan cp;
   if (!macro_cluster_plan(H, &cp)) return cudaErrorNotSupported;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(1u << cp.cbits, (unsigned)rows, 1);
-  cfg.blockDim = dim3((unsigned)cp.threads, 1, 1);
-  cfg.dynamicSmemBytes = cp.smem;
-  cfg.stream = st;
+  const ClusterConst K = cluster_const(H, cp);
   cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = 1u << cp.cbits;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  static std::atomic<unsigned long long> attr_done[4];
-  const int smax = 2 * 4 * kClusterMaxLocal * (int)sizeof(float2);
-#define RP_LAUNCH_CLUSTER(K)                                                                       \
-  {                                                                                                \
-    cudaError_t e = smem_attr_once((const void*)k_macro_cluster<K>, smax, attr_done[K - 1]);      \
-    if (e != cudaSuccess) return e;                                                                \
-    e = cudaLaunchKernelEx(&cfg, k_macro_cluster<K>, H, fields, row_field, row_win, macro,        \
-                           macro_dev, P, Q, X, coef, n_c, Zslot, cp.cbits, xblk);                  \
-    if (e != cudaSuccess) return e;                                                                \
+  cudaLaunchConfig_t cfg = cluster_cfg(cp, rows, st, at);
+  cudaError_t e = cudaSuccess;
+#define RP_CL(LB_, CB_, N1_, KPT_, I_)                                                            \
+  e = cluster_attr<LB_, CB_, N1_, KPT_>(g_cluster_attr[I_]);                                      \
+  if (e == cudaSuccess)                                                                            \
+    e = cudaLaunchKernelEx(&cfg, k_macro_cluster<LB_, CB_, N1_, KPT_>, K, H, fields, row_field,   \
+                           row_win, macro, macro_dev, P, Q, X, coef, n_c, Zslot, xblk);
+  switch (cluster_instance(cp, H)) {
+    case 0: RP_CL(-1, -1, -1, 1, 0) break;
+    case 1: RP_CL(-1, -1, -1, 2, 1) break;
+    case 2: RP_CL(-1, -1, -1, 3, 2) break;
+    default: RP_CL(5, 3, 4, 3, 3) break;
   }
-  switch (cp.kpt) {
-    case 1: RP_LAUNCH_CLUSTER(1) break;
-    case 2: RP_LAUNCH_CLUSTER(2) break;
-    case 3: RP_LAUNCH_CLUSTER(3) break;
-    default: RP_LAUNCH_CLUSTER(4) break;
-  }
-#undef RP_LAUNCH_CLUSTER
+#undef RP_CL
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
+}
+
+bool macro_cluster_default(const HamDev<float>& H) {
+  ClusterPlan cp;
+  return macro_cluster_plan(H, &cp) && cluster_instance(cp, H) == 3;
 }
 
 int macro_cluster_max_active(const HamDev<float>& H) {
   ClusterPlan cp;
   if (!macro_cluster_plan(H, &cp)) return 0;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(1u << cp.cbits, 1, 1);
-  cfg.blockDim = dim3((unsigned)cp.threads, 1, 1);
-  cfg.dynamicSmemBytes = cp.smem;
   cudaLaunchAttribute at[1];
-  at[0].id = cudaLaunchAttributeClusterDimension;
-  at[0].val.clusterDim.x = 1u << cp.cbits;
-  at[0].val.clusterDim.y = 1;
-  at[0].val.clusterDim.z = 1;
-  cfg.attrs = at;
-  cfg.numAttrs = 1;
-  static std::atomic<unsigned long long> attr_done[4];
-  const int smax = 2 * 4 * kClusterMaxLocal * (int)sizeof(float2);
+  cudaLaunchConfig_t cfg = cluster_cfg(cp, 1, nullptr, at);
   int n = 0;
   cudaError_t e = cudaSuccess;
-  switch (cp.kpt) {
-    case 1:
-      e = smem_attr_once((const void*)k_macro_cluster<1>, smax, attr_done[0]);
-      if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n, k_macro_cluster<1>, &cfg);
-      break;
-    case 2:
-      e = smem_attr_once((const void*)k_macro_cluster<2>, smax, attr_done[1]);
-      if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n, k_macro_cluster<2>, &cfg);
-      break;
-    case 3:
-      e = smem_attr_once((const void*)k_macro_cluster<3>, smax, attr_done[2]);
-      if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n, k_macro_cluster<3>, &cfg);
-      break;
-    default:
-      e = smem_attr_once((const void*)k_macro_cluster<4>, smax, attr_done[3]);
-      if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n, k_macro_cluster<4>, &cfg);
-      break;
+#define RP_CL(LB_, CB_, N1_, KPT_, I_)                                                            \
+  e = cluster_attr<LB_, CB_, N1_, KPT_>(g_cluster_attr[I_]);                                      \
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n, k_macro_cluster<LB_, CB_, N1_, KPT_>, &cfg);
+  switch (cluster_instance(cp, H)) {
+    case 0: RP_CL(-1, -1, -1, 1, 0) break;
+    case 1: RP_CL(-1, -1, -1, 2, 1) break;
+    case 2: RP_CL(-1, -1, -1, 3, 2) break;
+    default: RP_CL(5, 3, 4, 3, 3) break;
   }
+#undef RP_CL
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;

@@ -135,8 +135,9 @@ cudaError_t launch_macro_small(const SysTab<T>& S, const HamDev<T>* one, int ani
 // thread-block cluster per row, the row's Chebyshev vectors in distributed
 // shared memory (see k_macro_cluster): reads psi from P, writes the propagated
 // psi to Q and the singlet slices to X (tensor-core layout if xblk).
-// macro_cluster_plan: whether the system fits (isotropic, Z / 2^c <= 3520 with
-// c <= min(3, n_half)), and the launch shape; macro_cluster_max_active:
+// macro_cluster_plan: whether the system fits (isotropic spin-1/2 and spin-1
+// nuclei, Z / 2^c <= 2688 with c <= min(3, n_half)), and the launch shape;
+// macro_cluster_max_active:
 // clusters of that shape that fit the device at once (0 if none or on error).
 struct ClusterPlan {
   int cbits = 0;    // log2 of the CTAs per cluster (per row)
@@ -146,6 +147,9 @@ struct ClusterPlan {
   size_t smem = 0;  // dynamic shared memory per CTA
 };
 bool macro_cluster_plan(const HamDev<float>& H, ClusterPlan* out);
+// Whether kernel = 0 takes the cluster path: the shapes with a compiled
+// instance (measured faster than the per-term kernels).
+bool macro_cluster_default(const HamDev<float>& H);
 int macro_cluster_max_active(const HamDev<float>& H);
 cudaError_t launch_macro_cluster(const HamDev<float>& H, const FieldDev<float>* fields,
                                  const int* row_field, const int2* row_win, int macro,

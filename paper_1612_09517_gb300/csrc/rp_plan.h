@@ -81,4 +81,9 @@ std::string plan_field(const HostSystem& s, double B_mT, double t_max, int n_che
 // in FP64.
 long long basis_draw(uint64_t seed, uint32_t pair, long long sample, long long Z);
 
+// Kernel path rp_yields takes for kernel = 0 on this system in FP32 (2: whole
+// macro-step in one CTA, 4: on a thread-block cluster, 1: per-term kernels),
+// and in *cluster_ok whether kernel = 4 applies to it (rp_api.cu).
+int default_kernel_fp32(const HostSystem& hs, bool* cluster_ok);
+
 }  // namespace rp

@@ -6,7 +6,9 @@
 //   kernel  1 = one launch per Chebyshev term, 3 = the same with the partner
 //           tiles staged by bulk copies (where the layout allows), 2 = a whole
 //           macro-step per launch with the row in shared memory (only where
-//           Z fits);
+//           Z fits), 4 = a whole macro-step per launch with the row in the
+//           distributed shared memory of a thread-block cluster (FP32
+//           isotropic systems that fit);
 //   n_cheb  terms per macro-step (the planner then picks the step h that
 //           meets the tolerance: more terms, longer steps, a larger
 //           n_cheb x n_cheb time-integral Gram and more singlet slices);
@@ -146,13 +148,18 @@ rp_status rp_tune(rp_system* s, double B, int rows, const rp_options* base, rp_o
   const long long small_max = o.precision == RP_FP64 ? 1024 : 2048;
   const std::vector<int> ncs = {32, 48, 64, 88};
   std::vector<Cand> cands;
-  // kernel 3 differs from 1 only where it stages partner tiles (FP32, >= 8 spin-1/2)
+  // kernel 3 differs from 1 only where it stages partner tiles (FP32, >= 8 spin-1/2);
+  // kernel 4 only where a row fits a thread-block cluster (FP32, isotropic)
   const bool staged = o.precision == RP_FP32 && s->hs.n_half >= 8;
+  bool cluster_ok = false;
+  const int default_kernel = o.precision == RP_FP32 ? rp::default_kernel_fp32(s->hs, &cluster_ok)
+                                                    : (Z <= small_max ? 2 : 1);
   for (int nc : ncs)
     for (int g = 0; g <= 1; ++g) {
       cands.push_back({1, nc, g});
       if (Z <= small_max) cands.push_back({2, nc, g});
       if (staged) cands.push_back({3, nc, g});
+      if (cluster_ok && Z > small_max) cands.push_back({4, nc, g});
     }
   const int kTrialMacro = 6;
   double best = -1.0, base_rate = -1.0;
@@ -178,7 +185,7 @@ rp_status rp_tune(rp_system* s, double B, int rows, const rp_options* base, rp_o
     }
     const double rate = (double)rows * t_trial / (ms * 1e-3);
     r.candidates++;
-    const bool is_base = c.kernel == (o.kernel ? o.kernel : (Z <= small_max ? 2 : 1)) &&
+    const bool is_base = c.kernel == (o.kernel ? o.kernel : default_kernel) &&
                          c.n_cheb == (o.n_cheb ? o.n_cheb : 88) &&
                          c.graph == o.graph;
     if (is_base) base_rate = rate;

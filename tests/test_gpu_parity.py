@@ -304,10 +304,13 @@ def test_kernel_paths_agree(prec):
 
 
 # systems the cluster macro-step kernel splits over 1, 2, 4 and 8 CTAs
-# (isotropic; spin-1/2, spin-1 and spin-3/2 nuclei; J and k_S != k_T)
+# (isotropic spin-1/2 and spin-1 nuclei; J and k_S != k_T; 1 to 3
+# configurations per thread)
 CLUSTER = [
-    ("c1_spin32", lambda: wl.random_isotropic(5, 4, two_I=[1, 1, 1, 2, 3, 1, 1, 1, 2], k_S=1.0,
-                                              k_T=3.0, J=0.2, seed=50)),            # Z = 2304
+    ("c1_kpt1", lambda: wl.random_isotropic(4, 4, two_I=[1, 1, 2, 1, 1, 2, 1, 2], k_S=1.5,
+                                            k_T=0.6, J=0.4, seed=49)),              # Z = 864
+    ("c1_kpt2", lambda: wl.random_isotropic(5, 4, two_I=[1, 1, 1, 2, 2, 1, 1, 1, 2], k_S=1.0,
+                                            k_T=3.0, J=0.2, seed=50)),              # Z = 1728
     ("c2_one_half", lambda: wl.random_isotropic(4, 4, two_I=[1, 2, 2, 2, 2, 2, 2, 2], k_S=0.5,
                                                 k_T=2.0, seed=51)),                 # Z = 4374
     ("c4", lambda: wl.random_isotropic(6, 5, two_I=[1, 1, 1, 1, 2, 2, 1, 1, 1, 2, 2], k_S=2.0,

@@ -1,0 +1,135 @@
+"""GPU parity at full size and long horizons against stored oracle yields.
+
+The expected per-sample yields phi_S, phi_T and survival (Eq. 22 truncated at
+T, Eqs. 13, 19 for the initial states) come from tests/golden/parity_long.json,
+written by tests/golden/make_parity_goldens.py, which calls only the FP64 CPU
+oracle (oracle.chebyshev.propagate_yields on oracle.coherent.sample_states,
+seed 0).  Cases:
+
+* config 2 (Z = 20736, k_S != k_T): samples 0-7 at 0, 16.7, 33.3 and 50 mT,
+  each over 100 macro-steps of the FP64 plan (8800 Chebyshev terms per row),
+  in FP64 (1e-10) and FP32 (1e-5);
+* config 3 (Z = 2359296, anisotropic, J != 0): two rows at 2.5 and 10 mT over
+  0.1 us, FP32 and FP64;
+* the paper's model (Table I, Z = 2^20): two rows at 3.5 and 10 mT over
+  0.1 us, FP32 and FP64.
+
+phi_T is derived by conservation (1 - survival - phi_S), so its error is
+measured on the scale of the yields, max(|phi_T|, |phi_S|); survival is
+compared in absolute terms.  A slow test (RP_SLOW=1) compares the FP32 path
+with the FP64 path over the full 20 us horizon of config 2 at 16 fields x 8
+samples and prints the worst errors.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1612_09517_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLDEN = os.path.join(HERE, "golden", "parity_long.json")
+TOL = {"fp64": 1e-10, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    torch.cuda.set_device(0)
+    from paper_1612_09517_gb300 import rp
+    rp.use_torch_allocator()
+    yield
+
+
+def _cases(system):
+    doc = json.load(open(GOLDEN))
+    return [c for c in doc["cases"] if c["system"] == system]
+
+
+def _errors(got, c):
+    eS = abs(got[0] - c["phi_S"]) / abs(c["phi_S"])
+    eT = abs(got[1] - c["phi_T"]) / max(abs(c["phi_T"]), abs(c["phi_S"]))
+    eU = abs(got[2] - c["survival"])
+    return eS, eT, eU
+
+
+def _system(name):
+    if name == "config2":
+        return wl.config2().system
+    if name == "config3":
+        return wl.config3().system
+    from oracle.spin import GAMMA_E  # the golden file's system: the oracle's gamma_e
+    return wl.table1(GAMMA_E)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_config2_long_horizon_matches_oracle(prec):
+    """Config 2, 8 samples x 4 fields spanning 0-50 mT, >= 100 macro-steps per
+    row, in the default launch form (all samples of a field together)."""
+    from paper_1612_09517_gb300 import rp
+    cases = _cases("config2")
+    assert len(cases) == 32
+    sy = rp.System(wl.config2().system)
+    worst = 0.0
+    for B in sorted({c["B"] for c in cases}):
+        cs = sorted((c for c in cases if c["B"] == B), key=lambda c: c["sample"])
+        T = cs[0]["T"]
+        plan = sy.plan(B, T, precision=0 if prec == "fp64" else 1)
+        assert plan["n_macro"] >= (100 if prec == "fp64" else 80), plan["n_macro"]
+        r = sy.yields([B], 8, 0, T, per_sample=True, precision=prec)
+        for c in cs:
+            e = _errors(r["per_sample"][0, c["sample"]], c)
+            assert max(e) < TOL[prec], (B, c["sample"], e)
+            worst = max(worst, e[0], e[1])
+    print(f"config2 {prec}: worst relative error {worst:.2e}")
+
+
+@pytest.mark.parametrize("system", ["config3", "table1"])
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_full_size_rows_match_oracle(system, prec):
+    """Config 3 (anisotropic, Z = 2359296) and the paper's model problem
+    (Z = 2^20): two rows, several macro-steps, against the oracle."""
+    from paper_1612_09517_gb300 import rp
+    cases = _cases(system)
+    assert len(cases) == 2
+    sy = rp.System(_system(system))
+    fields = [c["B"] for c in cases]
+    T = cases[0]["T"]
+    r = sy.yields(fields, 2, 0, T, per_sample=True, precision=prec)
+    for i, c in enumerate(cases):
+        e = _errors(r["per_sample"][i, c["sample"]], c)
+        assert max(e) < TOL[prec], (system, c["B"], e)
+
+
+@pytest.mark.skipif(os.environ.get("RP_SLOW") != "1", reason="slow: set RP_SLOW=1 (~6 min)")
+def test_config2_fp32_vs_fp64_full_horizon():
+    """FP32 against FP64 over the full 20 us horizon of config 2: 16 fields
+    (every fourth of the 64-field sweep) x 8 samples.  The FP64 path is pinned
+    to the oracle above; this bounds the FP32 path's accumulated error over
+    up to 3259 macro-steps (287k Chebyshev terms per row)."""
+    from paper_1612_09517_gb300 import rp
+    w = wl.config2()
+    sy = rp.System(w.system)
+    fields = w.fields[::4]
+    r64 = sy.yields(fields, 8, 0, w.t_max, per_sample=True, precision="fp64")
+    b = r64["per_sample"]
+    for kernel in (0, 1):  # the default path (cluster kernel) and the per-term kernels
+        r32 = sy.yields(fields, 8, 0, w.t_max, per_sample=True, precision="fp32", kernel=kernel)
+        a = r32["per_sample"]
+        eS = np.abs(a[..., 0] - b[..., 0]) / np.abs(b[..., 0])
+        eT = np.abs(a[..., 1] - b[..., 1]) / np.maximum(np.abs(b[..., 1]), np.abs(b[..., 0]))
+        eU = np.abs(a[..., 2] - b[..., 2])
+        print(json.dumps({"kernel": kernel, "fields_mT": [round(float(x), 3) for x in fields],
+                          "samples": 8, "t_max_us": w.t_max, "worst_rel_phi_S": float(eS.max()),
+                          "worst_rel_phi_T_yield_scale": float(eT.max()),
+                          "worst_abs_survival": float(eU.max()),
+                          "worst_rel_phi_S_per_field": [float(x) for x in eS.max(axis=1)],
+                          "fp64_device_ms": r64["stats"]["device_ms"],
+                          "fp32_device_ms": r32["stats"]["device_ms"]}))
+        assert eS.max() < 1e-5 and eT.max() < 1e-5 and eU.max() < 1e-5
