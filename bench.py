@@ -5,25 +5,32 @@ Workload (config 2 of this project): 12 nuclei (8 spin-1/2 + 4 spin-1, 7 on
 radical 1 and 5 on radical 2, Z = 20736, state dimension 82944), isotropic
 a ~ N(0, 0.5 mT), J = 0, k_S = 2 us^-1, k_T = 0.5 us^-1 (decay not factorable),
 64 fields in 0-50 mT, horizon T = 20 us, complex FP32 state with FP64 time
-integrals and averages.
+integrals and averages; target SE <= 1e-3 at every field (Eq. 23).
 
-One step = one rp_yields call through the C ABI on a batch of the workload's
-(field, sample) units: the fields of ``--field-indices`` (default 1-6 of the 64,
-0.8-4.8 mT, where the per-sample spread of phi_S peaks) times
+One step = one rp_yields call through the C ABI on half of the 64 fields
+(alternate halves: fields 0, 2, 4, ... then 1, 3, 5, ...) x
 ``--samples-per-step`` coherent-state samples each, every sample propagated
-over the full horizon.  Steps use disjoint sample ranges (sample_offset),
-ranks too.  The cost of one Chebyshev term does not depend on the field (same
-Z, same kernels), so the measured terms per second carry over to every field.
+over the full horizon; steps and ranks use disjoint sample ranges
+(sample_offset).  The timed steps give (a) the throughput in Chebyshev
+row-terms per second on the curve's own field mix and (b) the spread sigma_f
+of phi_S at every field, pooled over the timed steps.
 
-Reported ``value``: seconds to the converged 64-field curve (SE <= 1e-3 at
-every field, Eq. 23) = sum_f M_f x (Chebyshev terms of one sample at field f,
-exact from the plan) / (measured terms per second), where M_f are the
-per-field sample counts rp_yields_converged uses for the measured per-field
-spread (SIGMA_PROFILE).  ``python bench.py --converge`` runs that whole
-converged curve once and prints its measured wall time (142.9 s on GB300).  ``value``
-uses device time of the calls (CUDA events on the call's stream, inputs and
-work buffers resident); ``e2e`` uses the wall time of the same C-ABI calls
-with host buffers (planning, host<->device copies and synchronisation inside).
+Reported ``value``: seconds to the converged 64-field curve =
+sum_f M_f x (Chebyshev terms of one sample at field f, exact from the plan) /
+(measured row-terms per second of device time), with M_f the per-field sample
+counts rp_yields_converged asks for the measured sigma_f
+(max(8, ceil(1.15 sigma_f^2 / SE^2) + 1)).  ``e2e`` is the same with the wall
+time of the C-ABI calls (host planning, host<->device copies and
+synchronisation inside).  At one GPU the line also carries, measured once
+each after the timed steps:
+* ``converged_measured``: the whole 64-field curve through rp_yields_converged
+  and through rp_yields_cv (learned control variate), wall time;
+* ``fp64_plain.measured_reduced``: the plain FP64 form against the FP32 +
+  control-variate form end to end on a reduced workload (4 fields, 1 us);
+  ``fp64_plain.projected_full`` projects the FP64 form to the full curve from
+  its measured throughput;
+* ``cpu_baseline``: the FP64 oracle on the host cores, bounded sample,
+  projected to the same curve.
 
 ``--impl reference`` times the FP64 CPU oracle (matrix-free Chebyshev,
 NumPy) on the host cores on bounded samples of the same workload and reports
@@ -54,11 +61,11 @@ WORKLOAD = ("config2: 12 nuclei (8x1/2 + 4x1, split 7/5), Z=20736, isotropic a~N
 SE_TARGET = 1e-3
 # Per-field standard deviation of phi_S over the 64 fields of this workload,
 # measured on GB300 by `python bench.py --converge` (rp_yields_converged,
-# SE <= 1e-3 everywhere; 16 to 991 samples per field, profiles/converged_config2_fp32.md).
-# Both arms turn their measured throughput into the time for a converged curve
-# with the same per-field sample counts M_f = max(8, ceil(1.15 sigma_f^2 / SE^2) + 1);
-# the CPU arm cannot afford enough full-horizon samples to measure sigma itself.
-SIGMA_PROFILE = [
+# SE <= 1e-3 everywhere; 16 to 991 samples per field).  Only the reference
+# arm uses it: the CPU oracle cannot afford enough full-horizon samples to
+# measure the spread itself, so it turns its throughput into the time for a
+# converged curve with these per-field sample counts.
+SIGMA_REFERENCE = [
     0.01636, 0.02267, 0.02981, 0.02294, 0.01538, 0.0101, 0.00761, 0.00606, 0.00459, 0.00434,
     0.00371, 0.00346, 0.00296, 0.00253, 0.00227, 0.00203, 0.00183, 0.00164, 0.00146, 0.00132,
     0.00119, 0.00109, 0.00099, 0.00091, 0.00085, 0.0008, 0.00076, 0.00074, 0.00071, 0.0007,
@@ -67,10 +74,9 @@ SIGMA_PROFILE = [
     0.00056, 0.00056, 0.00055, 0.00055, 0.00055, 0.00055, 0.00055, 0.00055, 0.00055, 0.00055,
     0.00056, 0.00056, 0.00056, 0.00056]
 M_MIN = 8
-SIGMA_REF = max(SIGMA_PROFILE)
 
 
-def samples_per_field(sigmas=SIGMA_PROFILE):
+def samples_per_field(sigmas=SIGMA_REFERENCE):
     """M_f of rp_yields_converged for SE <= SE_TARGET (Eq. 23), per field."""
     return [max(M_MIN, int(math.ceil(1.15 * s * s / (SE_TARGET * SE_TARGET))) + 1) for s in sigmas]
 
@@ -90,18 +96,17 @@ def _kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def _profile_traffic():
-    """DRAM bytes per row-term of the step kernel from the committed ncu summary,
-    or None when absent or taken on a different kernel source."""
-    p = os.path.join(ROOT, "profiles", "k_cheb_step_config2_fp32.md")
+def _profile_traffic(kernel):
+    """DRAM bytes (read + write) per row of one launch of `kernel` from the
+    committed ncu figures (profiles/traffic.json), or None when absent or
+    captured on a different kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
-    txt = open(p).read()
-    mh = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", txt)
-    mt = re.search(r"dram_bytes_per_row_term:\s*([0-9.eE+]+)", txt)
-    if not mh or not mt or mh.group(1) != _kernel_source_hash():
+    d = json.load(open(p)).get(kernel)
+    if not d or d.get("kernel_source_sha256_16") != _kernel_source_hash():
         return None
-    return float(mt.group(1))
+    return float(d["dram_bytes_per_row"])
 
 
 class ClockSampler:
@@ -171,14 +176,6 @@ def _curve_terms(sy, fields, t_max, precision):
     return sum(_field_terms(sy, fields, t_max, precision))
 
 
-def _m_needed(per_field_samples):
-    """M_needed = max over fields of (sigma_f / SE_target)^2 (Eq. 23)."""
-    import numpy as np
-    sig = [float(np.std(x, ddof=1)) for x in per_field_samples if len(x) > 1]
-    smax = max(sig)
-    return max(2, int(math.ceil((smax / SE_TARGET) ** 2))), smax
-
-
 # ---------------------------------------------------------------- CPU oracle
 
 def _oracle_worker(args):
@@ -236,10 +233,14 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--field-indices", default="1,2,3,4,5,6",
-                    help="indices into the 64-field sweep run in each step")
-    ap.add_argument("--samples-per-step", type=int, default=43)
+    ap.add_argument("--samples-per-step", type=int, default=2,
+                    help="samples per field in each step (each step runs half of the 64 fields)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the measured converged curves, the reduced FP64 comparison and "
+                         "the CPU baseline")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--kernel", type=int, default=0,
+                    help="rp_options.kernel of the timed steps and the profiling cases (0: choose)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--converge", action="store_true",
                     help="run the whole converged curve (rp_yields_converged, SE <= 1e-3) once "
@@ -453,26 +454,28 @@ def main():
     if args.ncu_case:
         # config-2 system, 3 fields x 64 samples = 192 rows (127 MB per state
         # vector, ~2 GB on the device), horizon of two macro-steps at 50 mT
-        o = rp.rp_default_options(precision=rp.RP_FP32, stream=torch.cuda.current_stream().cuda_stream)
+        o = rp.rp_default_options(precision=rp.RP_FP32, stream=torch.cuda.current_stream().cuda_stream,
+                                  kernel=args.kernel)
         h50 = sy.plan(50.0, w.t_max, precision=rp.RP_FP32)["h"]
         rp.rp_yields(sy.handle, np.array([0.0, 25.0, 50.0]), 64, 0, 2 * h50, o)
         torch.cuda.synchronize()
         return
-    idx = np.array([int(x) for x in args.field_indices.split(",")])
-    fields = w.fields[idx]
+    n_f = len(w.fields)
+    # two interleaved halves of the 64-field sweep; step i runs half i % 2
+    halves = [np.arange(g, n_f, 2) for g in range(2)]
     m = args.samples_per_step
     stream = torch.cuda.current_stream()
     fterms = _field_terms(sy, w.fields, w.t_max, prec)
     curve_terms = sum(fterms)
-    Mf = samples_per_field()
-    conv_terms = sum(m * t for m, t in zip(Mf, fterms))
 
     def step(i, profile):
+        idx = halves[i % 2]
         o = rp.rp_default_options(precision=prec, sample_offset=(i * world + rank) * m,
-                                  profile=int(profile), stream=stream.cuda_stream)
+                                  profile=int(profile), stream=stream.cuda_stream,
+                                  kernel=args.kernel)
         t0 = time.perf_counter()
-        r = rp.rp_yields(sy.handle, fields, m, 0, w.t_max, o, per_sample=True)
-        return r, time.perf_counter() - t0
+        r = rp.rp_yields(sy.handle, w.fields[idx], m, 0, w.t_max, o, per_sample=True)
+        return idx, r, time.perf_counter() - t0
 
     for i in range(args.warmup):
         step(i, False)
@@ -482,11 +485,13 @@ def main():
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    samples = [[] for _ in fields]
+    # per-field sums of phi_S over the timed steps: n, sum, sum of squares
+    acc = np.zeros((n_f, 3))
     dev_ms, wall_s, row_terms, launches = 0.0, 0.0, 0, 0
     step_ms, step_bytes, step_launches_timed = 0.0, 0.0, 0
     h2d = 0
     d2h = 0
+    paths = set()
     barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -494,7 +499,7 @@ def main():
         t_all = time.perf_counter()
         ev0.record(stream)
         for i in range(args.warmup, args.warmup + args.steps):
-            r, wall = step(i, True)
+            idx, r, wall = step(i, True)
             st = r["stats"]
             dev_ms += st["device_ms"]
             wall_s += wall
@@ -503,78 +508,128 @@ def main():
             step_ms += st["step_ms"]
             step_bytes += st["step_bytes"]
             step_launches_timed += st["step_launches_timed"]
-            h2d += st["h2d_bytes"] + fields.nbytes
+            paths.add(st["kernel_path"])
+            h2d += st["h2d_bytes"] + w.fields[idx].nbytes
             d2h += st["d2h_bytes"]
-            for j in range(len(fields)):
-                samples[j].extend(r["per_sample"][j, :, 0].tolist())
+            phi = r["per_sample"][:, :, 0]
+            acc[idx, 0] += phi.shape[1]
+            acc[idx, 1] += phi.sum(axis=1)
+            acc[idx, 2] += (phi * phi).sum(axis=1)
         ev1.record(stream)
         barrier()
         t_all = time.perf_counter() - t_all
     region_ms = ev0.elapsed_time(ev1)
     clocks = clk.summary()
 
-    # max over ranks of the timed quantities, sums of work
+    # max over ranks of the timed quantities, sums of work and of the samples
     row_terms_all, launches_all = row_terms, launches
     if world > 1:
         from paper_1612_09517_gb300 import shard
-        dev_ms, wall_s, region_ms = shard.max_over_ranks([dev_ms, wall_s, region_ms]).tolist()
+        dev_ms, wall_s, region_ms, step_ms = shard.max_over_ranks(
+            [dev_ms, wall_s, region_ms, step_ms]).tolist()
         work = torch.tensor([row_terms, launches], dtype=torch.float64, device="cuda")
         torch.distributed.all_reduce(work, op=torch.distributed.ReduceOp.SUM)
         row_terms_all, launches_all = work[0].item(), work[1].item()
+        a = torch.tensor(acc, dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(a, op=torch.distributed.ReduceOp.SUM)
+        acc = a.cpu().numpy()
 
-    m_live, sigma_live = _m_needed(samples)
-    sigma_max = max(SIGMA_PROFILE)
+    sigma, sigma_src = _sigma_from_sums(acc)
+    Mf = samples_per_field(sigma)
+    conv_terms = sum(mf * t for mf, t in zip(Mf, fterms))
+    sigma_max = max(sigma)
     m_uniform = max(2, int(math.ceil((sigma_max / SE_TARGET) ** 2)))
     rate_dev = row_terms_all / (dev_ms * 1e-3)
     rate_e2e = row_terms_all / wall_s
     value = conv_terms / rate_dev
     e2e = conv_terms / rate_e2e
 
-    # plain FP64 form on the same GPU, measured on a short horizon (per-term cost
-    # does not depend on the horizon) with the same row count
+    extras = rank == 0 and world == 1 and not args.no_extras
+    peak, peak_src = _peaks()
+    path = max(paths) if paths else 1
+    n_c = r["stats"]["n_cheb"]
+    if path == 4:
+        # on-chip macro-steps: the Chebyshev vectors stream through shared
+        # memory; algorithmic shared-memory bytes per configuration and term
+        # (phi_{n-1} and phi_{n-2} of the configuration, 16 B per flip-flop
+        # partner, phi_n written)
+        nh = int(np.sum(w.system.two_I == 1))
+        n1 = int(np.sum(w.system.two_I == 2))
+        b_cfg = 96.0 + 16.0 * (nh + 4.0 / 3.0 * n1)
+        sm_bytes = row_terms * (n_c - 1) / n_c * sy.Z * b_cfg
+        n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+        mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+        peak_sm = n_sm * 128.0 * mhz * 1e6 / 1e9
+        achieved = sm_bytes / (step_ms * 1e-3) / 1e9 if step_ms > 0 else None
+        traffic = _profile_traffic("k_macro_cluster")
+        rows_per_launch = row_terms / n_c / max(step_launches_timed, 1)
+        roofline = {
+            "bound": "smem", "kernel": "k_macro_cluster (whole macro-step, vectors in "
+                                      "distributed shared memory)",
+            "achieved": achieved, "peak": peak_sm, "unit": "GB/s",
+            "frac": (achieved / peak_sm) if achieved else None,
+            "traffic": (traffic * rows_per_launch) if traffic else None,
+            "peak_source": f"derived: {n_sm} SMs x 128 B/clk x {mhz:.0f} MHz (median SM clock "
+                           "in the timed region)",
+            "algorithmic_bytes_per_launch": sm_bytes / max(step_launches_timed, 1),
+            "algorithmic_bytes_per_config_term": b_cfg,
+            "avg_launch_ms": step_ms / max(step_launches_timed, 1),
+            "hbm_algorithmic_GBps": step_bytes / (step_ms * 1e-3) / 1e9 if step_ms > 0 else None,
+            "hbm_peak": peak, "hbm_peak_source": peak_src,
+        }
+    else:
+        achieved = step_bytes / (step_ms * 1e-3) / 1e9 if step_ms > 0 else None
+        traffic_per_row = _profile_traffic("k_cheb_step")
+        avg_rows = row_terms / max(step_launches_timed, 1) / n_c * (n_c - 1) \
+            if step_launches_timed else None
+        roofline = {
+            "bound": "hbm", "kernel": "k_cheb_step (fused H.psi + Chebyshev term)",
+            "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": (traffic_per_row * avg_rows) if (traffic_per_row and avg_rows) else None,
+            "peak_source": peak_src,
+            "algorithmic_bytes_per_launch": step_bytes / max(step_launches_timed, 1),
+            "avg_launch_ms": step_ms / max(step_launches_timed, 1),
+        }
+
+    # plain FP64 form on the same GPU: measured end to end on a reduced
+    # workload beside the spec form, and projected to the full curve
     fp64 = None
-    if args.precision == "fp32":
-        o = rp.rp_default_options(precision=rp.RP_FP64, stream=stream.cuda_stream)
-        rp.rp_yields(sy.handle, fields, m, 0, 0.02, o)
+    if args.precision == "fp32" and rank == 0:
+        o64 = rp.rp_default_options(precision=rp.RP_FP64, stream=stream.cuda_stream)
+        rp.rp_yields(sy.handle, w.fields[1:7], 43, 0, 0.02, o64)
         torch.cuda.synchronize()
-        r64 = rp.rp_yields(sy.handle, fields, m, 0, 0.2, o)
-        st = r64["stats"]
-        rate64 = st["row_terms"] * world / (st["device_ms"] * 1e-3)
+        r64 = rp.rp_yields(sy.handle, w.fields[1:7], 43, 0, 0.2, o64)
+        st64 = r64["stats"]
+        rate64 = st64["row_terms"] / (st64["device_ms"] * 1e-3)
         curve64 = _curve_terms(sy, w.fields, w.t_max, rp.RP_FP64)
         t64 = m_uniform * curve64 / rate64
-        fp64 = {"time_to_converged_s": t64, "row_terms_per_s": rate64,
-                "form": "FP64, same M at every field (M = (sigma_max / 1e-3)^2), no refill",
-                "ratio_ours_over_fp64_plain": value / t64}
+        fp64 = {"projected_full": {
+            "time_to_converged_s": t64, "row_terms_per_s": rate64,
+            "form": "FP64, one M for every field (M = (sigma_max / 1e-3)^2 from the sigma "
+                    "measured in the timed steps), rate measured over 0.2 us of 258 rows",
+            "ratio_ours_over_fp64_plain": value / t64}}
+        if extras:
+            fp64["measured_reduced"] = _reduced_ratio(rp, sy, w, stream)
 
-    peak, peak_src = _peaks()
-    achieved = step_bytes / (step_ms * 1e-3) / 1e9 if step_ms > 0 else None
-    rows = r["stats"]["rows"]
-    traffic_per_term = _profile_traffic()
-    avg_rows = row_terms / max(step_launches_timed, 1) / r["stats"]["n_cheb"] * (r["stats"]["n_cheb"] - 1) \
-        if step_launches_timed else None
-    roofline = {
-        "bound": "hbm", "kernel": "k_cheb_step (fused H.psi + Chebyshev term)",
-        "achieved": achieved, "peak": peak, "unit": "GB/s",
-        "frac": (achieved / peak) if achieved else None,
-        "traffic": (traffic_per_term * avg_rows) if (traffic_per_term and avg_rows) else None,
-        "peak_source": peak_src,
-        "algorithmic_bytes_per_launch": step_bytes / max(step_launches_timed, 1),
-        "avg_launch_ms": step_ms / max(step_launches_timed, 1),
-    }
+    converged = None
+    if extras:
+        converged = _converged_runs(rp, sy, w, prec, stream)
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if extras and not args.no_cpu_baseline:
         cores = os.cpu_count() or 1
         T_sample = 0.1
         B_list = list(w.fields[[0, 21, 42, 63]])
         rate_cpu, wall_cpu, terms_cpu = cpu_oracle_throughput(cores, T_sample, B_list)
-        conv_o = sum(m * t for m, t in zip(Mf, _oracle_field_terms(w.t_max, w.fields)))
+        conv_o = sum(mf * t for mf, t in zip(Mf, _oracle_field_terms(w.t_max, w.fields)))
         cpu = {"value": conv_o / rate_cpu, "unit": "s", "cores": cores,
                "kind": "oracle",
                "sample": f"{cores} spawned processes, each one (field, sample) FP64 matrix-free "
                          f"propagation over {T_sample} us (B in {[round(float(b), 1) for b in B_list]} mT); "
                          f"{rate_cpu:.0f} row-terms/s over {wall_cpu:.1f} s, extrapolated to "
-                         f"the {conv_o} oracle terms of the converged curve (per-field M_f)"}
+                         f"the {conv_o} oracle terms of the converged curve (per-field M_f from "
+                         "the sigma measured in the timed steps)"}
 
     if rank == 0:
         line = {
@@ -583,12 +638,15 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": "c64 state / f64 integrals" if args.precision == "fp32" else "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "step_fields_mT": [round(float(b), 3) for b in fields],
-                       "samples_per_step_per_rank": m, "rows": rows,
-                       "l2": "working set per step > 129 MB L2 (state vectors + Gram buffers)",
-                       "se_target": SE_TARGET, "samples_converged_curve": int(sum(Mf)),
+            "config": {"workload": WORKLOAD,
+                       "step": f"rp_yields on 32 of the 64 fields (alternate halves) x {m} "
+                               "samples per rank, full 20 us horizon",
+                       "samples_per_step_per_rank": m, "rows": r["stats"]["rows"],
+                       "kernel_path": path,
+                       "l2": "working set per step > 129 MB L2 (state vectors + singlet slices)",
+                       "se_target": SE_TARGET, "sigma_source": sigma_src,
+                       "sigma_max": sigma_max, "samples_converged_curve": int(sum(Mf)),
                        "terms_converged_curve": int(conv_terms),
-                       "sigma_live_step_fields": sigma_live, "sigma_profile_max": sigma_max,
                        "uniform_M": m_uniform,
                        "uniform_M_time_s": m_uniform * curve_terms / rate_dev,
                        "curve_terms_per_sample": curve_terms,
@@ -598,12 +656,89 @@ def main():
             "gpu_launches": int(launches_all),
             "roofline": roofline,
             "clocks": clocks,
+            "converged_measured": converged,
             "fp64_plain": fp64,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def _sigma_from_sums(acc):
+    """Per-field sample standard deviation of phi_S (M - 1 denominator) from
+    (n, sum, sum of squares); a field without two samples takes its nearest
+    measured neighbour's value."""
+    import numpy as np
+    n, s1, s2 = acc[:, 0], acc[:, 1], acc[:, 2]
+    sig = np.full(len(n), np.nan)
+    ok = n >= 2
+    sig[ok] = np.sqrt(np.maximum(s2[ok] - s1[ok] ** 2 / n[ok], 0.0) / (n[ok] - 1))
+    src = (f"measured in the timed steps: {int(n[ok].min()) if ok.any() else 0}-"
+           f"{int(n.max())} samples per field")
+    if not ok.all():
+        good = np.flatnonzero(ok)
+        for f in np.flatnonzero(~ok):
+            sig[f] = sig[good[np.argmin(np.abs(good - f))]]
+        src += f"; {int((~ok).sum())} fields without samples take the nearest field's value"
+    return [float(x) for x in sig], src
+
+
+def _converged_runs(rp, sy, w, prec, stream):
+    """The converged 64-field curve measured end to end through the C ABI:
+    rp_yields_converged (plain, per-field sample counts) and rp_yields_cv (the
+    learned control variate where it pays); seed 7 (directions independent of
+    the timed steps)."""
+    import torch
+    out = {}
+    o = rp.rp_default_options(precision=prec, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = rp.rp_yields_converged(sy.handle, w.fields, SE_TARGET, M_MIN, 4000, 7, w.t_max, o)
+    wall = time.perf_counter() - t0
+    out["plain"] = {"wall_s": wall, "device_s": r["stats"]["device_ms"] * 1e-3,
+                    "samples": int(r["M_used"].sum()), "max_SE": float(r["out"][:, 2].max()),
+                    "row_terms": r["stats"]["row_terms"], "kernel_path": r["stats"]["kernel_path"]}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    c = rp.rp_yields_cv(sy.handle, w.fields, SE_TARGET, M_MIN, 4000, 7, w.t_max, o,
+                        rp.rp_cv_default_plan())
+    wall = time.perf_counter() - t0
+    out["cv"] = {"wall_s": wall, "samples_plain": int(c["M_plain"].sum()),
+                 "samples_cv": int(c["M_cv"].sum()), "max_SE": float(c["out"][:, 1].max()),
+                 "fields_with_cv": int(c["out"][:, 7].sum())}
+    out["note"] = ("one run each, after the timed steps, 64 fields to SE <= 1e-3 (Eq. 23); "
+                   "wall time of the C-ABI call")
+    return out
+
+
+def _reduced_ratio(rp, sy, w, stream):
+    """The ratio the goal names, measured end to end on a reduced workload:
+    the four fields 0.79-3.17 mT of the sweep over t_max = 1 us to SE <= 1e-3,
+    FP32 + control variate (rp_yields_cv) against the plain FP64 form
+    (rp_yields_converged in FP64), and plain FP32 beside them."""
+    import torch
+    fields = w.fields[1:5]
+    T = 1.0
+    res = {"workload": "config-2 system, fields " + str([round(float(b), 3) for b in fields]) +
+                       " mT, t_max = 1 us, SE <= 1e-3 at every field"}
+    for name, prec, cv in (("fp64_plain", rp.RP_FP64, False), ("fp32_plain", rp.RP_FP32, False),
+                           ("fp32_cv", rp.RP_FP32, True)):
+        o = rp.rp_default_options(precision=prec, stream=stream.cuda_stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if cv:
+            r = rp.rp_yields_cv(sy.handle, fields, SE_TARGET, M_MIN, 4000, 11, T, o,
+                                rp.rp_cv_default_plan())
+            se = float(r["out"][:, 1].max())
+        else:
+            r = rp.rp_yields_converged(sy.handle, fields, SE_TARGET, M_MIN, 4000, 11, T, o)
+            se = float(r["out"][:, 2].max())
+        res[name] = {"wall_s": time.perf_counter() - t0, "max_SE": se}
+    res["ratio_fp32_cv_over_fp64_plain"] = res["fp32_cv"]["wall_s"] / res["fp64_plain"]["wall_s"]
+    res["ratio_fp32_plain_over_fp64_plain"] = (res["fp32_plain"]["wall_s"] /
+                                               res["fp64_plain"]["wall_s"])
+    return res
 
 
 if __name__ == "__main__":

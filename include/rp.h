@@ -131,6 +131,8 @@ typedef struct rp_stats {
   long long d2h_bytes;          /* device-to-host bytes copied by the call */
   long long graph_launches;     /* macro-steps replayed from a CUDA graph (graph = 1);
                                    their kernels are counted in kernel_launches */
+  int kernel_path;              /* kernel path of the Chebyshev terms (rp_options.kernel
+                                   values 1-4; rp_yields and rp_yields_converged) */
 } rp_stats;
 
 /* Propagation plan of one field (rp_plan_field; host logic, no GPU needed). */

@@ -455,6 +455,10 @@ class YieldEngine {
 
   void set_seed(uint64_t seed) { seed_ = seed; }
 
+  // Kernel path taken (rp_stats.kernel_path): 4 cluster, 2 one CTA per row,
+  // 3 staged per-term, 1 per-term.
+  int kernel_path() const { return cluster_ ? 4 : (small_ ? 2 : (o_.kernel == 3 ? 3 : 1)); }
+
   // Time-resolved sums (launch_trace) after every macro-step; eager launches.
   void set_trace(double* trace) { d_trace_ = trace; }
 
@@ -646,6 +650,7 @@ void fill_stats(rp_stats* stats, const YieldEngine<T>& eng, long long items, int
   stats->propagations = items;
   stats->rows = R;
   stats->n_cheb = n_c;
+  stats->kernel_path = eng.kernel_path();
   float ms = 0.f;
   ck(cudaEventElapsedTime(&ms, ev0, ev1), "cudaEventElapsedTime");
   stats->device_ms = ms;
