@@ -15,7 +15,12 @@ computes, in plain NumPy FP64 from the definitions:
 * the loss 1/(2n) sum (g - y)^2 and its gradient by the chain rule
   (silu'(z) = s(z) (1 + z (1 - s(z))), s = logistic);
 * the control-variate estimate mean(phi - beta (g - mu)), beta = cov(phi, g) /
-  var(g), with standard error sqrt(var(phi - beta g)/M + beta^2 var(mu)).
+  var(g), with standard error sqrt(var(phi - beta g)/M + beta^2 var(mu));
+* one training step of Adam (D. P. Kingma and J. Ba, "Adam: a method for
+  stochastic optimization", ICLR 2015, Algorithm 1: bias-corrected first and
+  second moment estimates) with decoupled weight decay on the weights
+  (I. Loshchilov and F. Hutter, "Decoupled weight decay regularization",
+  ICLR 2019): theta <- theta - lr wd theta - lr m_hat / (sqrt(v_hat) + eps).
 
 Parameters are a flat vector in the order W_0, b_0, W_1, b_1, ..., W_L, b_L,
 W_l row-major of shape (out, in).
@@ -117,3 +122,28 @@ def cv_estimate(phi, g, mu, var_mu):
     resid = phi - beta * g
     se = np.sqrt(resid.var(ddof=1) / M + beta * beta * var_mu)
     return est, se, beta
+
+
+def adam_step(params, m, v, grad, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, wd=0.0,
+              decay_mask=None):
+    """One Adam update at step t >= 1 (Kingma and Ba, Algorithm 1) with
+    decoupled weight decay wd on the entries where decay_mask is true.
+    Returns the new (params, m, v)."""
+    params = np.asarray(params, float)
+    grad = np.asarray(grad, float)
+    m = beta1 * np.asarray(m, float) + (1.0 - beta1) * grad
+    v = beta2 * np.asarray(v, float) + (1.0 - beta2) * grad * grad
+    m_hat = m / (1.0 - beta1 ** t)
+    v_hat = v / (1.0 - beta2 ** t)
+    decay = np.zeros_like(params) if decay_mask is None else np.where(decay_mask, wd, 0.0)
+    new = params - lr * decay * params - lr * m_hat / (np.sqrt(v_hat) + eps)
+    return new, m, v
+
+
+def weight_mask(d_in, hidden, layers):
+    """True on the weight entries of the flat parameter vector, False on biases."""
+    out = []
+    for (r, c) in shapes(d_in, hidden, layers):
+        out.append(np.ones(r * c, bool))
+        out.append(np.zeros(r, bool))
+    return np.concatenate(out)

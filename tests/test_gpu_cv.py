@@ -60,6 +60,36 @@ def test_loss_and_gradient_match_reference():
     assert np.max(np.abs(g - rg)) <= 1e-4 * np.max(np.abs(rg))
 
 
+def test_adam_training_steps_match_reference():
+    """Two full-batch epochs of rp_cv_train (two Adam steps on the FP32 master
+    parameters, gradients through the BF16 weights, targets standardised per
+    field) against the reference: loss gradient (mlp.loss_and_grad) and Adam
+    with decoupled weight decay (mlp.adam_step, Kingma and Ba's update)."""
+    lr, wd = 1e-2, 1e-2
+    s, sy, cv = _net(hidden=16, layers=2, epochs=2, batch=64, lr=lr, weight_decay=wd)
+    d_in = cv.d_in
+    p0 = cv.get_params().astype(np.float64)
+    samples = np.arange(200, 264)
+    B = np.full(64, 2.0)
+    phi = 0.3 + 0.05 * np.sin(np.arange(64) * 0.7)
+    cv.train(B, samples, 77, phi)
+    got = cv.get_params().astype(np.float64)
+    x = mlp.features(77, 0, samples, s, 2.0, 10.0).astype(np.float32).astype(np.float64)
+    y = ((phi - phi.mean()) / phi.std(ddof=1)).astype(np.float32).astype(np.float64)
+    mask = mlp.weight_mask(d_in, 16, 2)
+    p, m, v = p0, np.zeros_like(p0), np.zeros_like(p0)
+    for t in (1, 2):
+        fwd = _bf16_weights(p, d_in, 16, 2).astype(np.float64)
+        _, grad = mlp.loss_and_grad(fwd, x, y, d_in, 16, 2)
+        p, m, v = mlp.adam_step(p.astype(np.float32).astype(np.float64), m, v, grad, t, lr,
+                                wd=wd, decay_mask=mask)
+    err = np.abs(got - p)
+    # a wrong bias correction moves the first step by 0.316 lr; a missing decay by lr wd |theta|
+    assert np.quantile(err, 0.999) < 1e-3 * lr, np.sort(err)[-5:]
+    assert err.max() < 2 * lr
+    assert np.max(np.abs(got - p0)) > 1.5 * lr  # two steps were taken
+
+
 def test_eval_and_mean_match_reference():
     """Features from the device Philox map + forward pass = reference forward."""
     s, sy, cv = _net(hidden=16, layers=2)

@@ -72,3 +72,34 @@ def test_control_variate_estimator_limits():
     g = phi + noise  # rho^2 = 1/2
     est, se, beta = mlp.cv_estimate(phi, g, 0.4, 0.0)
     assert abs(se ** 2 / (phi.var(ddof=1) / M) - 0.5) < 0.03
+
+
+def test_adam_step_closed_forms():
+    """Adam's bias correction and the decoupled weight decay, from their
+    definitions: (i) a constant gradient g gives m_hat = g and v_hat = g^2 at
+    every step, so each step moves by exactly lr g / (|g| + eps) (without the
+    correction the first step would be sqrt(1 - beta2) / (1 - beta1) = 0.316
+    of it); (ii) a zero gradient leaves only the decay, theta (1 - lr wd), on
+    the weights and nothing on the biases; (iii) on the quadratic
+    f = |theta|^2 / 2 the first step is lr sign(theta)."""
+    rng = np.random.default_rng(5)
+    th = rng.normal(size=40)
+    g = rng.normal(size=40)
+    m = np.zeros(40)
+    v = np.zeros(40)
+    p = th.copy()
+    lr, eps = 1e-2, 1e-8
+    for t in range(1, 8):
+        p_new, m, v = mlp.adam_step(p, m, v, g, t, lr, eps=eps)
+        assert np.allclose(p - p_new, lr * g / (np.abs(g) + eps), rtol=1e-12, atol=1e-15)
+        p = p_new
+    mask = mlp.weight_mask(3, 4, 2)
+    assert mask.size == sum(r * c + r for r, c in mlp.shapes(3, 4, 2))
+    assert mask.sum() == 3 * 4 + 4 * 4 + 4 * 1
+    th = rng.normal(size=mask.size)
+    p1, m1, v1 = mlp.adam_step(th, np.zeros_like(th), np.zeros_like(th), np.zeros_like(th), 1,
+                               0.1, wd=0.5, decay_mask=mask)
+    assert np.allclose(p1[mask], th[mask] * (1 - 0.05), rtol=1e-15)
+    assert np.array_equal(p1[~mask], th[~mask])
+    q, _, _ = mlp.adam_step(th, np.zeros_like(th), np.zeros_like(th), th, 1, 0.03)
+    assert np.allclose(th - q, 0.03 * th / (np.abs(th) + 1e-8), rtol=1e-12)
