@@ -79,7 +79,18 @@ typedef struct rp_options {
                              2: M basis states |S, M> drawn uniformly at random
                              (rp_basis_indices) instead of coherent states, an
                              unbiased estimate of the same trace (rp_yields and
-                             rp_time_trace only) */
+                             rp_time_trace only);
+                             3: the trace of Eq. 14 regrouped by J_z sector
+                             (rp_yields, isotropic systems): propagation i
+                             carries the normalised sum of the i-th basis state
+                             |S, m> of every class of nuclear configurations
+                             with the same total M.  H, K and P_S conserve J_z
+                             (field along z, isotropic couplings), so the
+                             cross terms between classes vanish and the
+                             propagation's yield is the mean of its n_i states';
+                             the trace is sum_i (n_i / Z) phi_i over the
+                             largest class's size of propagations
+                             (rp_trace_propagations) instead of Z */
   long long sample_offset;/* first sample index (resume / sharding) */
   uint32_t pair_id;       /* Philox counter word 3 (radical-pair id) */
   int profile;            /* 1: time the H.psi step kernels with CUDA events */
@@ -213,8 +224,10 @@ rp_status rp_plan_field(const rp_system* sys, double B, double t_max, int precis
  *   t_max       horizon T > 0 (us)
  *   opt         NULL for defaults
  *   out         [n_fields * 5] host: Phi_S, Phi_T, SE_S, SE_T, mean survival
+ *               (deterministic = 3: the trace, SE 0)
  *   per_sample  [n_fields * M * 3] host or NULL: phi_S, phi_T, survival of
- *               each (field, sample), field-major (M = Z when deterministic)
+ *               each (field, sample), field-major (M = rp_trace_propagations
+ *               when deterministic is 1 or 3)
  *   stats       optional host output
  * Every sample uses the same directions at every field (common random numbers).
  * Errors: RP_EINVAL, RP_ENOMEM, RP_ECUDA, RP_ENOTCONV, RP_ENODEV. */
@@ -425,6 +438,13 @@ rp_status rp_basis_indices(uint64_t seed, uint32_t pair_id, long long sample_off
 rp_status rp_time_trace(rp_system* sys, double B, int M, uint64_t seed, double t_max,
                         const rp_options* opt, int max_times, int* n_times, double* t,
                         double* out);
+
+/* Propagations per field of a deterministic trace (host only): Z for
+ * deterministic = 1 (Eq. 14), the size of the largest class of nuclear
+ * configurations with equal total M for deterministic = 3 (the J_z-sector
+ * regrouping; isotropic systems only).  rp_yields with these modes writes
+ * that many per-sample entries per field.  Errors: RP_EINVAL, RP_ENOMEM. */
+rp_status rp_trace_propagations(const rp_system* sys, int deterministic, long long* n);
 
 /* Launch-configuration autotuner (the paper has no counterpart: its method
  * ran serially on CPUs).  For one system, precision and concurrency it times

@@ -307,7 +307,8 @@ class YieldEngine {
     }
     d_err_ = ar_.get<int>(1);
     ck(cudaMemsetAsync(d_err_, 0, sizeof(int), st_), "cudaMemsetAsync");
-    S_ = rp::SysTab<T>{d_ham_, d_lay_, d_kS_, row_sys_, Zslot_, o_.pair_id, d_pair_, d_err_};
+    S_ = rp::SysTab<T>{d_ham_, d_lay_, d_kS_, row_sys_, Zslot_, o_.pair_id, d_pair_, d_err_,
+                       sec_rank_, sec_scale_};
     rows_.field = ar_.get<int>(R);
     rows_.win = ar_.get<int2>(R);
     rows_.sample = ar_.get<long long>(R);
@@ -455,6 +456,12 @@ class YieldEngine {
 
   void set_seed(uint64_t seed) { seed_ = seed; }
 
+  // J_z-sector tables of deterministic = 3 (device arrays; before alloc_rows).
+  void set_sectors(const int* rank, const double* scale) {
+    sec_rank_ = rank;
+    sec_scale_ = scale;
+  }
+
   // Kernel path taken (rp_stats.kernel_path): 4 cluster, 2 one CTA per row,
   // 3 staged per-term, 1 per-term.
   int kernel_path() const { return cluster_ ? 4 : (small_ ? 2 : (o_.kernel == 3 ? 3 : 1)); }
@@ -570,6 +577,8 @@ class YieldEngine {
   rp::HamDev<T> ham1_{};
   bool small_ = false;
   bool cluster_ = false;
+  const int* sec_rank_ = nullptr;
+  const double* sec_scale_ = nullptr;
   bool tc_gram_ = false;
   int n_sm_ = 0;
   rp::SysTab<T> S_{};
@@ -619,7 +628,7 @@ std::vector<Item> make_items(const std::vector<rp::FieldPlan>& plans, const std:
   for (int f : forder)
     for (long long s = first[f]; s < first[f] + count[f]; ++s)
       items.push_back(Item{f,
-                           sm.mode == 1   ? s
+                           (sm.mode == 1 || sm.mode == 3) ? s
                            : sm.mode == 2 ? rp::basis_draw(sm.seed, sm.pair, sample_offset + s, sm.Z)
                                           : sample_offset + s,
                            out0[f] + (s - first[f]), (int)plans[f].n_macro,
@@ -692,7 +701,11 @@ rp_status run_yields(rp_system* sys, int n_fields, const double* fields, int M, 
   const double tol = o.tol > 0 ? o.tol : default_tol(o.precision);
   if (n_c % 4 != 0 || n_c < 8 || n_c > 88)
     return fail(RP_EINVAL, "n_cheb must be a multiple of 4 in [8, 88]");
-  const long long Mr = o.deterministic == 1 ? hs.Z : (long long)M;
+  // J_z-sector trace: propagation i carries the i-th basis state of every
+  // nuclear-M class, normalised; it counts n_i / Z in the trace (Eq. 14)
+  std::vector<int> sec_rank, sec_n;
+  const long long n_sec = o.deterministic == 3 ? rp::sector_table(hs, &sec_rank, &sec_n) : 0;
+  const long long Mr = o.deterministic == 1 ? hs.Z : (o.deterministic == 3 ? n_sec : (long long)M);
   std::vector<rp::FieldPlan> plans;
   rp_status ps = plan_all(hs, n_fields, fields, t_max, n_c, tol, plans);
   if (ps != RP_OK) return ps;
@@ -711,6 +724,22 @@ rp_status run_yields(rp_system* sys, int n_fields, const double* fields, int M, 
     eng.set_seed(seed);
     ck(cudaEventRecord(ev.a, st), "cudaEventRecord");
     eng.set_fields(plans);
+    double* d_w = nullptr;
+    if (o.deterministic == 3) {
+      int* d_rank = ar.get<int>(sec_rank.size());
+      double* d_scale = ar.get<double>((size_t)n_sec);
+      d_w = ar.get<double>((size_t)n_sec);
+      std::vector<double> scale((size_t)n_sec), w((size_t)n_sec);
+      for (long long i = 0; i < n_sec; ++i) {
+        scale[(size_t)i] = 1.0 / std::sqrt((double)sec_n[(size_t)i]);
+        w[(size_t)i] = (double)sec_n[(size_t)i] / (double)hs.Z;
+      }
+      ck(cudaMemcpyAsync(d_rank, sec_rank.data(), sec_rank.size() * sizeof(int), cudaMemcpyHostToDevice, st), "h2d sectors");
+      ck(cudaMemcpyAsync(d_scale, scale.data(), scale.size() * sizeof(double), cudaMemcpyHostToDevice, st), "h2d sectors");
+      ck(cudaMemcpyAsync(d_w, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice, st), "h2d sectors");
+      eng.h2d += (long long)(sec_rank.size() * sizeof(int) + 2 * scale.size() * sizeof(double));
+      eng.set_sectors(d_rank, d_scale);
+    }
     eng.alloc_rows(R);
     double* d_ps = ar.get<double>((size_t)n_items * 3);
     double* d_stats = ar.get<double>((size_t)n_fields * 5);
@@ -723,7 +752,11 @@ rp_status run_yields(rp_system* sys, int n_fields, const double* fields, int M, 
     }
     ck(cudaMemcpyAsync(d_off, offcnt.data(), offcnt.size() * sizeof(long long), cudaMemcpyHostToDevice, st), "h2d");
     eng.h2d += (long long)(offcnt.size() * sizeof(long long));
-    ck(rp::launch_stats(d_ps, d_off, d_off + n_fields, n_fields, d_stats, st), "stats kernel");
+    if (o.deterministic == 3)
+      ck(rp::launch_stats_weighted(d_ps, d_off, d_off + n_fields, d_w, n_fields, d_stats, st),
+         "weighted stats kernel");
+    else
+      ck(rp::launch_stats(d_ps, d_off, d_off + n_fields, n_fields, d_stats, st), "stats kernel");
     eng.launches++;
     ck(cudaMemcpyAsync(out, d_stats, (size_t)n_fields * 5 * sizeof(double), cudaMemcpyDeviceToHost, st), "d2h stats");
     d2h += (long long)n_fields * 5 * sizeof(double);
@@ -1454,8 +1487,11 @@ rp_status rp_yields(rp_system* s, int n_fields, const double* fields, int M, uin
   if (n_fields < 0) return fail(RP_EINVAL, "n_fields must be >= 0");
   if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
   if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..4, gram 0..2 and graph 0 or 1");
-  if (o.deterministic < 0 || o.deterministic > 2) return fail(RP_EINVAL, "deterministic must be 0, 1 or 2");
-  if (o.deterministic != 1 && M < 2) return fail(RP_EINVAL, "M must be >= 2 (the standard error needs it)");
+  if (o.deterministic < 0 || o.deterministic > 3) return fail(RP_EINVAL, "deterministic must be 0, 1, 2 or 3");
+  if (o.deterministic == 3 && s->hs.aniso)
+    return fail(RP_EINVAL, "the J_z-sector trace (deterministic = 3) needs isotropic hyperfine couplings");
+  if ((o.deterministic == 0 || o.deterministic == 2) && M < 2)
+    return fail(RP_EINVAL, "M must be >= 2 (the standard error needs it)");
   if (!(t_max > 0.0) || !std::isfinite(t_max)) return fail(RP_EINVAL, "t_max must be positive and finite");
   if (o.sample_offset < 0) return fail(RP_EINVAL, "sample_offset must be >= 0");
   if (n_fields > 0 && (!fields || !out)) return fail(RP_EINVAL, "NULL fields or out");
@@ -1485,6 +1521,25 @@ rp_status rp_basis_indices(uint64_t seed, uint32_t pair_id, long long sample_off
   return RP_OK;
 }
 
+rp_status rp_trace_propagations(const rp_system* s, int deterministic, long long* n) {
+  g_err.clear();
+  if (!s || !n) return fail(RP_EINVAL, "system or n is NULL");
+  if (deterministic == 1) {
+    *n = s->hs.Z;
+    return RP_OK;
+  }
+  if (deterministic != 3) return fail(RP_EINVAL, "deterministic must be 1 or 3");
+  if (s->hs.aniso)
+    return fail(RP_EINVAL, "the J_z-sector trace (deterministic = 3) needs isotropic hyperfine couplings");
+  try {
+    std::vector<int> rank, n_of;
+    *n = rp::sector_table(s->hs, &rank, &n_of);
+  } catch (const std::bad_alloc&) {
+    return fail(RP_ENOMEM, "host allocation failed");
+  }
+  return RP_OK;
+}
+
 rp_status rp_time_trace(rp_system* s, double B, int M, uint64_t seed, double t_max,
                         const rp_options* opt, int max_times, int* n_times, double* t,
                         double* out) {
@@ -1495,6 +1550,7 @@ rp_status rp_time_trace(rp_system* s, double B, int M, uint64_t seed, double t_m
   if (!s || !n_times) return fail(RP_EINVAL, "system or n_times is NULL");
   if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
   if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..4, gram 0..2 and graph 0 or 1");
+  if (o.deterministic == 3) return fail(RP_ENOTIMPL, "rp_time_trace does not take the J_z-sector trace (deterministic = 3)");
   if (o.deterministic < 0 || o.deterministic > 2) return fail(RP_EINVAL, "deterministic must be 0, 1 or 2");
   if (o.deterministic != 1 && M < 1) return fail(RP_EINVAL, "M must be >= 1");
   if (!(t_max > 0.0) || !std::isfinite(t_max)) return fail(RP_EINVAL, "t_max must be positive and finite");

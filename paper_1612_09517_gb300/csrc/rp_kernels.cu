@@ -1500,6 +1500,37 @@ __global__ void __launch_bounds__(256) k_stats(const double* __restrict__ per_sa
   }
 }
 
+// Deterministic trace from weighted propagations (Eq. 14 regrouped by J_z
+// sector): out[f] = sum_i w_i (phi_S, phi_T, survival)_i, standard errors 0.
+__global__ void __launch_bounds__(256) k_stats_weighted(const double* __restrict__ per_sample,
+                                                        const long long* __restrict__ off,
+                                                        const long long* __restrict__ cnt,
+                                                        const double* __restrict__ w,
+                                                        double* __restrict__ out) {
+  __shared__ double sh[256];
+  const int f = blockIdx.x;
+  const double* p = per_sample + (size_t)off[f] * 3;
+  const long long M = cnt[f];
+  double s0 = 0, s1 = 0, s2 = 0;
+  for (long long i = threadIdx.x; i < M; i += blockDim.x) {
+    s0 += w[i] * p[3 * i];
+    s1 += w[i] * p[3 * i + 1];
+    s2 += w[i] * p[3 * i + 2];
+  }
+  const double m0 = block_sum<256>(s0, sh);
+  __syncthreads();
+  const double m1 = block_sum<256>(s1, sh);
+  __syncthreads();
+  const double m2 = block_sum<256>(s2, sh);
+  if (threadIdx.x == 0) {
+    out[5 * f + 0] = m0;
+    out[5 * f + 1] = m1;
+    out[5 * f + 2] = 0.0;
+    out[5 * f + 3] = 0.0;
+    out[5 * f + 4] = m2;
+  }
+}
+
 // ---- Philox4x32-10 (Salmon et al., SC'11) and coherent states (Eq. 15) ----
 
 __device__ __forceinline__ void philox4x32_10(uint32_t (&c)[4], uint32_t k0, uint32_t k1) {
@@ -1589,7 +1620,11 @@ __global__ void __launch_bounds__(256) k_init_state(const SysTab<T> S,
   if (m >= L.Z) return;
   T* psi = (row_win && (row_win[r].x & 1)) ? S1 : S0;
   double pr = 1.0, pi = 0.0;
-  if (deterministic) {
+  if (deterministic == 3) {
+    // propagation i carries the i-th state |S, m> of every nuclear-M class
+    const long long i = row_sample[r];
+    pr = (S.sec_rank[m] == i) ? S.sec_scale[i] : 0.0;
+  } else if (deterministic) {
     pr = (m == row_sample[r]) ? 1.0 : 0.0;
   } else {
     const double* A = amps + (size_t)r * kMaxNucDev * 10 * 2;
@@ -1937,6 +1972,14 @@ cudaError_t launch_stats(const double* per_sample, const long long* off, const l
                          int n_fields, double* out, cudaStream_t st) {
   if (n_fields == 0) return cudaSuccess;
   k_stats<<<n_fields, 256, 0, st>>>(per_sample, off, cnt, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_stats_weighted(const double* per_sample, const long long* off,
+                                  const long long* cnt, const double* w, int n_fields,
+                                  double* out, cudaStream_t st) {
+  if (n_fields == 0) return cudaSuccess;
+  k_stats_weighted<<<n_fields, 256, 0, st>>>(per_sample, off, cnt, w, out);
   return cudaGetLastError();
 }
 

@@ -83,6 +83,10 @@ struct SysTab {
   uint32_t pair_base;
   const uint32_t* pair_of;
   int* err = nullptr;  // device error word (bit 0: a bounded wait gave up), may be NULL
+  // J_z-sector superposition (deterministic = 3): rank of every configuration
+  // within its nuclear-M class, and 1/sqrt(n_i) of propagation i (n_i states)
+  const int* sec_rank = nullptr;
+  const double* sec_scale = nullptr;
 };
 
 // ---- launchers (return cudaGetLastError after the launch) ----
@@ -204,6 +208,13 @@ cudaError_t launch_finalize(const SysTab<T>& S, const RowsDev& R, int rows, doub
 // per_sample[off[f] .. off[f] + cnt[f]).
 cudaError_t launch_stats(const double* per_sample, const long long* off, const long long* cnt,
                          int n_fields, double* out, cudaStream_t st);
+
+// out[f] = (sum_i w_i phi_S, sum_i w_i phi_T, 0, 0, sum_i w_i survival) over
+// entry i of per_sample[off[f] .. off[f] + cnt[f]) (w has cnt[f] entries):
+// a deterministic trace assembled from weighted propagations.
+cudaError_t launch_stats_weighted(const double* per_sample, const long long* off,
+                                  const long long* cnt, const double* w, int n_fields,
+                                  double* out, cudaStream_t st);
 
 cudaError_t launch_zero(double* p, size_t n, cudaStream_t st);
 

@@ -347,4 +347,30 @@ long long basis_draw(uint64_t seed, uint32_t pair, long long sample, long long Z
   return idx;
 }
 
+long long sector_table(const HostSystem& hs, std::vector<int>* rank, std::vector<int>* n_of) {
+  // twice the nuclear M of configuration m: sum_p (2 I_p - 2 j_p) with digit
+  // j_p = I_p - M_p of position p (the layout's digits count down from +I_p)
+  int two_max = 0;
+  for (int p = 0; p < hs.n_nuc; ++p) two_max += hs.two_I[hs.order[p]];
+  std::vector<long long> count(2 * (size_t)two_max + 1, 0);
+  rank->assign((size_t)hs.Z, 0);
+  for (long long m = 0; m < hs.Z; ++m) {
+    int two_M = 0;
+    for (int p = 0; p < hs.n_nuc; ++p) {
+      const int d = hs.two_I[hs.order[p]] + 1;
+      const long long j = (m / hs.stride[p]) % d;
+      two_M += (d - 1) - 2 * (int)j;
+    }
+    long long& c_ = count[(size_t)(two_M + two_max)];
+    (*rank)[(size_t)m] = (int)c_;
+    ++c_;
+  }
+  long long n_prop = 0;
+  for (long long c_ : count) n_prop = std::max(n_prop, c_);
+  n_of->assign((size_t)n_prop, 0);
+  for (long long c_ : count)
+    for (long long i = 0; i < c_; ++i) (*n_of)[(size_t)i]++;
+  return n_prop;
+}
+
 }  // namespace rp

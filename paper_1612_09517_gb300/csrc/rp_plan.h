@@ -81,6 +81,13 @@ std::string plan_field(const HostSystem& s, double B_mT, double t_max, int n_che
 // in FP64.
 long long basis_draw(uint64_t seed, uint32_t pair, long long sample, long long Z);
 
+// J_z sectors of the nuclear basis (deterministic = 3): for every
+// configuration m (layout order) its rank within the class of configurations
+// with the same total nuclear M; n_of[i] = number of classes with more than i
+// members, i.e. the states that propagation i carries.  Returns the number of
+// propagations (the size of the largest class).
+long long sector_table(const HostSystem& hs, std::vector<int>* rank, std::vector<int>* n_of);
+
 // Kernel path rp_yields takes for kernel = 0 on this system in FP32 (2: whole
 // macro-step in one CTA, 4: on a thread-block cluster, 1: per-term kernels),
 // and in *cluster_ok whether kernel = 4 applies to it (rp_api.cu).

@@ -351,8 +351,10 @@ extern "C" rp_status rp_yields_static(rp_system* s, int n_fields, const double* 
   if (!s) return sfail(RP_EINVAL, "system is NULL");
   if (n_fields < 0) return sfail(RP_EINVAL, "n_fields must be >= 0");
   if (o.precision != RP_FP64 && o.precision != RP_FP32) return sfail(RP_EINVAL, "bad precision");
-  if (o.deterministic < 0 || o.deterministic > 2) return sfail(RP_EINVAL, "deterministic must be 0, 1 or 2");
-  if (o.deterministic > 1) return sfail(RP_ENOTIMPL, "basis-state sampling (deterministic = 2) is served by rp_yields");
+  if (o.deterministic < 0 || o.deterministic > 3) return sfail(RP_EINVAL, "deterministic must be 0, 1, 2 or 3");
+  if (o.deterministic > 1)
+    return sfail(RP_ENOTIMPL, "basis-state sampling (deterministic = 2) and the J_z-sector trace "
+                              "(deterministic = 3) are served by rp_yields");
   // this entry point runs the per-term kernels with the CUDA-core integral,
   // eagerly: other launch choices are refused rather than silently ignored
   if (o.kernel != 0 && o.kernel != 1) return sfail(RP_ENOTIMPL, "rp_yields_static runs kernel = 1 only (0 or 1 accepted)");

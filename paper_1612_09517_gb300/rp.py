@@ -143,6 +143,7 @@ SIGNATURES = [
                                    C.POINTER(rp_stats)]),
     ("rp_basis_indices", C.c_int, [C.c_uint64, C.c_uint32, C.c_longlong, C.c_int, C.c_longlong,
                                    C.POINTER(C.c_longlong)]),
+    ("rp_trace_propagations", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_longlong)]),
     ("rp_time_trace", C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_uint64, C.c_double,
                                 C.POINTER(rp_options), C.c_int, C.POINTER(C.c_int),
                                 C.POINTER(C.c_double), C.POINTER(C.c_double)]),
@@ -226,12 +227,19 @@ def rp_plan_field(h, B, t_max, precision=RP_FP64, n_cheb=0, tol=0.0, with_coef=F
     return d
 
 
+def rp_trace_propagations(h, deterministic):
+    """Propagations per field of the deterministic traces (1: Z, 3: J_z sectors)."""
+    n = C.c_longlong()
+    _check(LIB.rp_trace_propagations(h, int(deterministic), C.byref(n)))
+    return int(n.value)
+
+
 def rp_yields(h, fields, M, seed, t_max, opt=None, per_sample=False, Z=None):
     fields = np.ascontiguousarray(fields, dtype=np.float64).reshape(-1)
     nf = fields.size
     o = opt if opt is not None else rp_default_options()
     out = np.zeros(max(nf * 5, 1))
-    Mr = Z if o.deterministic == 1 else M
+    Mr = rp_trace_propagations(h, o.deterministic) if o.deterministic in (1, 3) else M
     ps = np.zeros(max(nf * Mr * 3, 1)) if per_sample else None
     stats = rp_stats()
     _check(LIB.rp_yields(h, nf, _dptr(fields), int(M), C.c_uint64(int(seed)), float(t_max),

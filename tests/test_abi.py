@@ -177,7 +177,7 @@ def test_option_validation_without_gpu():
     autotuner needs two rows; basis-index draws need a positive Z."""
     sy = rp.System(wl.config1().system)
     for kw, msg in ((dict(kernel=5), "kernel"), (dict(kernel=-1), "kernel"), (dict(gram=3), "gram"),
-                    (dict(graph=2), "graph"), (dict(deterministic=3), "deterministic")):
+                    (dict(graph=2), "graph"), (dict(deterministic=4), "deterministic")):
         with pytest.raises(rp.RPError, match=msg):
             sy.yields([0.0], 4, 0, 1.0, **kw)
     with pytest.raises(rp.RPError, match="rows"):
@@ -198,3 +198,25 @@ def test_static_entry_point_refuses_other_launch_choices_without_gpu():
                     (dict(max_rows=-1), "max_rows")):
         with pytest.raises(rp.RPError, match=msg):
             rp.rp_yields_static(sy.handle, [0.0], 4, 0, 1.0, rp.rp_default_options(**kw))
+
+
+def test_trace_propagations_count_sector_classes():
+    """deterministic = 3 needs as many propagations as the largest class of
+    nuclear configurations with equal total M (counted here by brute force);
+    deterministic = 1 needs Z; anisotropic systems are refused."""
+    import itertools
+    for s in (wl.config1().system, wl.config2().system,
+              wl.random_isotropic(2, 2, two_I=[1, 2, 3, 1], seed=3)):
+        sy = rp.System(s)
+        counts = {}
+        for ms in itertools.product(*[range(int(t) + 1) for t in s.two_I]):
+            two_M = sum(int(t) - 2 * j for t, j in zip(s.two_I, ms))
+            counts[two_M] = counts.get(two_M, 0) + 1
+        assert rp.rp_trace_propagations(sy.handle, 3) == max(counts.values())
+        assert rp.rp_trace_propagations(sy.handle, 1) == s.Z
+    assert rp.rp_trace_propagations(rp.System(wl.config1().system).handle, 3) == 6
+    an = rp.System(wl.random_anisotropic(1, 1, seed=2))
+    with pytest.raises(rp.RPError, match="isotropic"):
+        rp.rp_trace_propagations(an.handle, 3)
+    with pytest.raises(rp.RPError, match="isotropic"):
+        an.yields([0.0], 2, 0, 1.0, deterministic=3)

@@ -158,6 +158,55 @@ def test_deterministic_trace_matches_oracle():
     assert abs(r["out"][1, 0] - r["out"][2, 0]) < 1e-10
 
 
+SECTOR = [
+    ("config1", lambda: wl.config1().system),
+    ("spin1_J", lambda: wl.random_isotropic(2, 2, two_I=[1, 2, 1, 2], k_S=2.0, k_T=0.4, J=0.3,
+                                            seed=46)),
+    ("spin32", lambda: wl.random_isotropic(1, 2, two_I=[3, 1, 2], k_S=0.2, k_T=5.0, J=-0.5,
+                                           seed=41)),
+]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("name,mk", SECTOR, ids=[c[0] for c in SECTOR])
+def test_sector_trace_matches_oracle_and_basis_states(name, mk, prec):
+    """The J_z-sector trace (deterministic = 3) equals tr[Y P_S]/Z of the
+    oracle (Eq. 14) with fewer propagations, and each propagation's yield is
+    the mean of the yields of the basis states it carries (run one by one
+    with deterministic = 1): the cross terms between J_z classes vanish."""
+    rp = _rp()
+    s = mk()
+    sy = rp.System(s)
+    fields = np.array([0.0, 1.2, 4.0])
+    T = 2.5
+    r3 = sy.yields(fields, 2, 0, T, per_sample=True, precision=prec, deterministic=3)
+    r1 = sy.yields(fields, 2, 0, T, per_sample=True, precision=prec, deterministic=1)
+    n3 = rp.rp_trace_propagations(sy.handle, 3)
+    assert r3["per_sample"].shape == (3, n3, 3) and n3 < sy.Z
+    assert r3["stats"]["propagations"] == 3 * n3
+    tol = TOL[prec]
+    for i, B in enumerate(fields):
+        ref = dense.trace_yields(s, B, T)
+        assert abs(r3["out"][i, 0] - ref[0]) < tol * abs(ref[0])
+        assert abs(r3["out"][i, 1] - ref[1]) < tol * max(abs(ref[1]), abs(ref[0]))
+        assert abs(r3["out"][i, 4] - ref[2]) < tol
+        assert r3["out"][i, 2] == 0.0 and r3["out"][i, 3] == 0.0
+    # class of every layout configuration: total 2M from the layout digits
+    dims = [int(s.two_I[k]) + 1 for k in sy.order]
+    rank, seen = np.zeros(sy.Z, int), {}
+    for m in range(sy.Z):
+        q, two_M = m, 0
+        for d in dims:
+            two_M += (d - 1) - 2 * (q % d)
+            q //= d
+        rank[m] = seen.get(two_M, 0)
+        seen[two_M] = rank[m] + 1
+    for i in range(n3):
+        members = np.flatnonzero(rank == i)
+        want = r1["per_sample"][:, members, :].mean(axis=1)
+        assert np.allclose(r3["per_sample"][:, i, :], want, rtol=tol, atol=tol * 1e-2), i
+
+
 @pytest.mark.parametrize("kernel", [1, 2])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("name,mk", MIXED[1:], ids=[m[0] for m in MIXED[1:]])
