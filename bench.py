@@ -259,6 +259,10 @@ def parse():
                     help="config-2 system, 3 fields x 200 samples: spread of phi_S with "
                          "coherent-state samples vs random basis states (deterministic = 2); "
                          "one JSON line")
+    ap.add_argument("--trace", action="store_true",
+                    help="config 2 at 1.59 and 3.17 mT: the deterministic trace (Eq. 14) by J_z "
+                         "sectors against the stochastic estimate to SE <= 1e-3, measured wall "
+                         "times and the trace-level error; one JSON line")
     ap.add_argument("--ncu-case3", action="store_true",
                     help="profiling case of the anisotropic config-3 system (Z = 2359296): "
                          "2 rows, two macro-steps, ~4 GB on the device")
@@ -442,6 +446,35 @@ def main():
                           "device_ms": r["stats"]["device_ms"], "row_terms": r["stats"]["row_terms"],
                           "mean_survival": float(r["out"][:, 4].max()),
                           "M100": curve[100], "M200": curve[200], "hist": hist}), flush=True)
+        return
+    if args.trace:
+        fb = w.fields[[2, 4]]
+        o = rp.rp_default_options(precision=prec, stream=torch.cuda.current_stream().cuda_stream)
+        sy.yields([0.0], 2, 0, 0.05)  # warm-up
+        n3 = rp.rp_trace_propagations(sy.handle, 3)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        o3 = rp.rp_default_options(precision=prec, deterministic=3,
+                                   stream=torch.cuda.current_stream().cuda_stream)
+        tr = rp.rp_yields(sy.handle, fb, 2, 0, w.t_max, o3)
+        t_trace = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        st = rp.rp_yields_converged(sy.handle, fb, SE_TARGET, M_MIN, 4000, 3, w.t_max, o)
+        t_stoch = time.perf_counter() - t0
+        z = (st["out"][:, 0] - tr["out"][:, 0]) / st["out"][:, 2]
+        print(json.dumps({"mode": "trace", "workload": WORKLOAD, "fields_mT": fb.round(4).tolist(),
+                          "precision": args.precision, "Z": int(sy.Z), "sector_propagations": n3,
+                          "trace_PhiS": tr["out"][:, 0].tolist(), "trace_wall_s": t_trace,
+                          "trace_row_terms": tr["stats"]["row_terms"],
+                          "stochastic_PhiS": st["out"][:, 0].tolist(),
+                          "stochastic_SE": st["out"][:, 2].tolist(),
+                          "stochastic_M": st["M_used"].tolist(), "stochastic_wall_s": t_stoch,
+                          "z_stochastic_vs_trace": z.tolist(),
+                          "speedup_vs_sector_trace_measured": t_trace / t_stoch,
+                          "speedup_vs_full_trace_projected": t_trace * sy.Z / n3 / t_stoch,
+                          "note": "full trace (Z propagations per field) projected from the "
+                                  "sector trace by the exact ratio of propagations, Z / n3; "
+                                  "every propagation costs the same Chebyshev terms"}), flush=True)
         return
     if args.ncu_case3:
         w3 = wl.config3()

@@ -197,6 +197,16 @@ rp_status rp_create(int n_nuc, const int* radical, const int* two_I, const doubl
 /* Release a system (NULL is ignored). */
 void rp_destroy(rp_system* sys);
 
+/* The same radical pair with the field along the unit vector
+ * n(theta, phi) = (sin theta cos phi, sin theta sin phi, cos theta) instead of
+ * z (Eq. 1 with omega = |gamma_e| B n): a new system whose hyperfine tensors
+ * are R A_k R^T with R = R_y(-theta) R_z(-phi), the rotation that takes n to z
+ * (isotropic tensors are unchanged).  Yields and traces of the new system at
+ * field B are those of the original with the field B n; the coherent-state
+ * directions it samples are drawn in the rotated frame (the lab direction of
+ * a sample direction n_k is R^T n_k).  Host-only.  Errors: RP_EINVAL, RP_ENOMEM. */
+rp_status rp_rotate(const rp_system* sys, double theta, double phi, rp_system** out);
+
 /* Nucleus order of the state layout: order[p] = input index of the nucleus at
  * position p (p = 0 innermost); *Z_out = number of nuclear states.  Either
  * output may be NULL. */
@@ -438,6 +448,18 @@ rp_status rp_basis_indices(uint64_t seed, uint32_t pair_id, long long sample_off
 rp_status rp_time_trace(rp_system* sys, double B, int M, uint64_t seed, double t_max,
                         const rp_options* opt, int max_times, int* n_times, double* t,
                         double* out);
+
+/* Time-resolved expectation of an electron operator (Eq. 18 with A = A_e x 1
+ * on the nuclei; Eqs. 7-9): the sample mean of <psi(t)| A_e x 1 |psi(t)> at
+ * the macro-step boundaries of one field, with psi(t) the decaying wavepacket
+ * of Eq. 13 (so, as for P_S(t) in rp_time_trace, recombined population no
+ * longer contributes).  A_e is 4 x 4 complex, row-major, 32 doubles (re, im),
+ * in the electron basis e = 2 e_1 + e_2 (alpha = 0, beta = 1).
+ *   t    [n_times] host, us;  out [n_times * 2] host: Re, Im of the mean
+ * Other arguments, the size query and errors as rp_time_trace. */
+rp_status rp_time_observable(rp_system* sys, double B, int M, uint64_t seed, double t_max,
+                             const rp_options* opt, const double* A_e, int max_times,
+                             int* n_times, double* t, double* out);
 
 /* Propagations per field of a deterministic trace (host only): Z for
  * deterministic = 1 (Eq. 14), the size of the largest class of nuclear

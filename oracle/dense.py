@@ -44,9 +44,10 @@ def _vanloan_block(A, P, t):
     return F, F.conj().T @ E[:n, n:]
 
 
-def yield_operators(system, B, T, max_norm_step=0.5):
-    """(Y_S, Y_T, F) with Y_X = k_X int_0^T e^{A^H s} P_X e^{A s} ds and F = e^{A T}."""
-    A = generator(system, B)
+def yield_operators(system, B, T, max_norm_step=0.5, direction=None):
+    """(Y_S, Y_T, F) with Y_X = k_X int_0^T e^{A^H s} P_X e^{A s} ds and F = e^{A T};
+    the field is B along z, or along the unit vector `direction`."""
+    A = generator(system, B, direction)
     PS, PT = projectors(system)
     norm = max(np.abs(A).sum(axis=0).max(), 1.0)  # 1-norm of A
     n_double = max(0, int(math.ceil(math.log2(max(norm * T / max_norm_step, 1.0)))))
@@ -61,9 +62,9 @@ def yield_operators(system, B, T, max_norm_step=0.5):
     return system.k_S * YS, system.k_T * YT, F
 
 
-def sample_yields(system, B, T, psi0):
+def sample_yields(system, B, T, psi0, direction=None):
     """Per-sample (phi_S, phi_T, survival) for initial states psi0 (n, 4Z)."""
-    YS, YT, F = yield_operators(system, B, T)
+    YS, YT, F = yield_operators(system, B, T, direction=direction)
     psi0 = np.atleast_2d(psi0)
     phiS = np.einsum("si,ij,sj->s", psi0.conj(), YS, psi0).real
     phiT = np.einsum("si,ij,sj->s", psi0.conj(), YT, psi0).real
@@ -71,9 +72,9 @@ def sample_yields(system, B, T, psi0):
     return phiS, phiT, surv
 
 
-def trace_yields(system, B, T):
+def trace_yields(system, B, T, direction=None):
     """Deterministic trace (Eq. 14 with rho(0) = P_S/Z): (Phi_S, Phi_T, survival)."""
-    YS, YT, F = yield_operators(system, B, T)
+    YS, YT, F = yield_operators(system, B, T, direction=direction)
     PS, _ = projectors(system)
     Z = system.Z
     surv = np.trace(F.conj().T @ F @ PS).real / Z
@@ -96,3 +97,17 @@ def estimate(per_sample):
     x = np.asarray(per_sample, float)
     M = x.shape[-1]
     return x.mean(axis=-1), x.std(axis=-1, ddof=1) / math.sqrt(M)
+
+
+def expectation_traces(system, B, psi0, times, ops, direction=None):
+    """Eqs. 7-9 and 18 per initial state: <psi(t)| O |psi(t)> for each full-space
+    operator O in `ops` at each time, psi(t) = exp(A t) psi0 (Eq. 13), averaged
+    over the rows of psi0.  Returns an array (len(times), len(ops)), complex."""
+    A = generator(system, B, direction)
+    psi0 = np.atleast_2d(psi0)
+    out = np.zeros((len(times), len(ops)), complex)
+    for i, t in enumerate(times):
+        P = scipy.linalg.expm(A * float(t)) @ psi0.T  # (4Z, n)
+        for j, O in enumerate(ops):
+            out[i, j] = np.mean(np.einsum("in,ij,jn->n", P.conj(), O, P))
+    return out

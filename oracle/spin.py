@@ -66,13 +66,20 @@ def projectors(system):
     return 0.25 * one - dot, 0.75 * one + dot
 
 
-def hamiltonian(system, B):
-    """Eq. 1 as a dense matrix in rad/us, field B (mT) along z."""
+def hamiltonian(system, B, direction=None):
+    """Eq. 1 as a dense matrix in rad/us, field B (mT) along z, or along the
+    unit vector `direction` (the Zeeman term omega . S_i of Eq. 1 with
+    omega = |gamma_e| B direction)."""
     dims = dims_of(system)
     S1, S2 = electron_ops(system)
     S = (S1, S2)
     omega = GAMMA_E * float(B)
-    H = omega * (S1[2] + S2[2])
+    if direction is None:
+        H = omega * (S1[2] + S2[2])
+    else:
+        n = np.asarray(direction, float)
+        n = n / np.linalg.norm(n)
+        H = sum(omega * n[a] * (S1[a] + S2[a]) for a in range(3))
     H = H + 2.0 * GAMMA_E * system.J * sum(S1[a] @ S2[a] for a in range(3))
     for k in range(system.n_nuc):
         Ik = spin_matrices(int(system.two_I[k]))
@@ -92,9 +99,9 @@ def haberkorn(system):
     return 0.5 * system.k_S * PS + 0.5 * system.k_T * PT
 
 
-def generator(system, B):
+def generator(system, B, direction=None):
     """A = -i H - K, so that d psi/dt = A psi (Eq. 13, Eq. 6)."""
-    return -1j * hamiltonian(system, B) - haberkorn(system)
+    return -1j * hamiltonian(system, B, direction) - haberkorn(system)
 
 
 def singlet_vector():

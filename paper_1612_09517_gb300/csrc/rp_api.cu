@@ -415,7 +415,7 @@ class YieldEngine {
       row_terms += act * (long long)n_c_;
       if (d_trace_) {
         T* Sb2[2] = {S0_, S1_};
-        launched(rp::launch_trace<T>(S_, Sb2[(k + 1) & 1], rows_.win, k, R_, d_trace_, st_),
+        launched(rp::launch_trace<T>(S_, Sb2[(k + 1) & 1], rows_.win, k, R_, trace_op_, d_trace_, st_),
                  "trace kernel");
       }
       // rows whose window ends after this macro-step: finish and refill
@@ -466,8 +466,12 @@ class YieldEngine {
   // 3 staged per-term, 1 per-term.
   int kernel_path() const { return cluster_ ? 4 : (small_ ? 2 : (o_.kernel == 3 ? 3 : 1)); }
 
-  // Time-resolved sums (launch_trace) after every macro-step; eager launches.
-  void set_trace(double* trace) { d_trace_ = trace; }
+  // Time-resolved sums (launch_trace) after every macro-step, 4 doubles per
+  // time point, with an optional electron operator; eager launches.
+  void set_trace(double* trace, const rp::ElecOp& op) {
+    d_trace_ = trace;
+    trace_op_ = op;
+  }
 
   long long graph_launches = 0;
 
@@ -579,6 +583,7 @@ class YieldEngine {
   bool cluster_ = false;
   const int* sec_rank_ = nullptr;
   const double* sec_scale_ = nullptr;
+  rp::ElecOp trace_op_{};
   bool tc_gram_ = false;
   int n_sm_ = 0;
   rp::SysTab<T> S_{};
@@ -777,7 +782,8 @@ rp_status run_yields(rp_system* sys, int n_fields, const double* fields, int M, 
 // samples (or the Z basis states when deterministic).
 template <typename T>
 rp_status run_time_trace(rp_system* sys, double B, int M, uint64_t seed, double t_max,
-                         const rp_options& o, int n_times, double* t, double* out) {
+                         const rp_options& o, int n_times, double* t, double* out,
+                         const double* A_e = nullptr, double* obs = nullptr) {
   const rp::HostSystem& hs = sys->hs;
   cudaStream_t st = (cudaStream_t)o.stream;
   const int n_c = o.n_cheb > 0 ? o.n_cheb : default_ncheb(o.precision);
@@ -790,7 +796,15 @@ rp_status run_time_trace(rp_system* sys, double B, int M, uint64_t seed, double 
   const std::vector<Item> items = make_items(plans, first, count, out0, o.sample_offset,
                                              SampleMode{o.deterministic, seed, o.pair_id, hs.Z});
   const int R = choose_rows<T>(hs, o, n_c, (long long)items.size());
-  std::vector<double> h_tr(2 * (size_t)n_times, 0.0);
+  std::vector<double> h_tr(4 * (size_t)n_times, 0.0);
+  rp::ElecOp op{};
+  if (A_e) {
+    for (int q = 0; q < 16; ++q) {
+      op.re[q] = A_e[2 * q];
+      op.im[q] = A_e[2 * q + 1];
+    }
+    op.on = 1;
+  }
   {
     Arena ar(st);
     YieldEngine<T> eng({&hs}, o, n_c, st, ar);
@@ -798,9 +812,9 @@ rp_status run_time_trace(rp_system* sys, double B, int M, uint64_t seed, double 
     eng.set_fields(plans);
     eng.alloc_rows(R);
     double* d_ps = ar.get<double>(items.size() * 3);
-    double* d_tr = ar.get<double>(2 * (size_t)n_times);
-    ck(cudaMemsetAsync(d_tr, 0, 2 * (size_t)n_times * sizeof(double), st), "cudaMemsetAsync");
-    eng.set_trace(d_tr);
+    double* d_tr = ar.get<double>(4 * (size_t)n_times);
+    ck(cudaMemsetAsync(d_tr, 0, 4 * (size_t)n_times * sizeof(double), st), "cudaMemsetAsync");
+    eng.set_trace(d_tr, op);
     eng.run(items, d_ps);
     ck(cudaMemcpyAsync(h_tr.data(), d_tr, h_tr.size() * sizeof(double), cudaMemcpyDeviceToHost, st),
        "d2h trace");
@@ -811,11 +825,31 @@ rp_status run_time_trace(rp_system* sys, double B, int M, uint64_t seed, double 
   for (int i = 0; i < n_times; ++i) {
     t[i] = i * h;
     // psi(0) = |S> x (normalised nuclear state): P_S = survival = 1, P_T = 0
-    const double p_s = i == 0 ? 1.0 : h_tr[2 * (size_t)i] / (double)Mr;
-    const double surv = i == 0 ? 1.0 : h_tr[2 * (size_t)i + 1] / (double)Mr;
-    out[3 * (size_t)i] = p_s;
-    out[3 * (size_t)i + 1] = surv - p_s;  // P_T = 1 - P_S on the electrons
-    out[3 * (size_t)i + 2] = surv;
+    const double p_s = i == 0 ? 1.0 : h_tr[4 * (size_t)i] / (double)Mr;
+    const double surv = i == 0 ? 1.0 : h_tr[4 * (size_t)i + 1] / (double)Mr;
+    if (out) {
+      out[3 * (size_t)i] = p_s;
+      out[3 * (size_t)i + 1] = surv - p_s;  // P_T = 1 - P_S on the electrons
+      out[3 * (size_t)i + 2] = surv;
+    }
+    if (obs) {
+      if (i == 0) {
+        // <S| A |S> for the normalised initial states
+        const double s = 0.70710678118654752440;
+        const double v[4] = {0.0, s, -s, 0.0};
+        double re = 0.0, im = 0.0;
+        for (int e = 0; e < 4; ++e)
+          for (int f = 0; f < 4; ++f) {
+            re += v[e] * A_e[2 * (4 * e + f)] * v[f];
+            im += v[e] * A_e[2 * (4 * e + f) + 1] * v[f];
+          }
+        obs[0] = re;
+        obs[1] = im;
+      } else {
+        obs[2 * (size_t)i] = h_tr[4 * (size_t)i + 2] / (double)Mr;
+        obs[2 * (size_t)i + 1] = h_tr[4 * (size_t)i + 3] / (double)Mr;
+      }
+    }
   }
   return RP_OK;
 }
@@ -1379,6 +1413,44 @@ rp_status rp_set_allocator(rp_alloc_fn a, rp_free_fn f, void* ctx) {
   return RP_OK;
 }
 
+rp_status rp_rotate(const rp_system* s, double theta, double phi, rp_system** out) {
+  g_err.clear();
+  if (!s || !out) return fail(RP_EINVAL, "system or out is NULL");
+  if (!std::isfinite(theta) || !std::isfinite(phi)) return fail(RP_EINVAL, "non-finite angle");
+  const rp::HostSystem& h = s->hs;
+  // R = R_y(-theta) R_z(-phi) takes n(theta, phi) to z; tensors A' = R A R^T
+  const double ct = std::cos(theta), st = std::sin(theta), cp = std::cos(phi), sp = std::sin(phi);
+  const double Rz[3][3] = {{cp, sp, 0.0}, {-sp, cp, 0.0}, {0.0, 0.0, 1.0}};
+  const double Ry[3][3] = {{ct, 0.0, -st}, {0.0, 1.0, 0.0}, {st, 0.0, ct}};
+  double Rm[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      Rm[i][j] = 0.0;
+      for (int q = 0; q < 3; ++q) Rm[i][j] += Ry[i][q] * Rz[q][j];
+    }
+  std::vector<double> A2((size_t)9 * h.n_nuc);
+  for (int k = 0; k < h.n_nuc; ++k) {
+    const double* A = &h.A[9 * k];
+    double* B = &A2[9 * (size_t)k];
+    const bool iso = A[1] == 0.0 && A[2] == 0.0 && A[3] == 0.0 && A[5] == 0.0 && A[6] == 0.0 &&
+                     A[7] == 0.0 && A[0] == A[4] && A[0] == A[8];
+    if (iso) {  // a multiple of the identity is invariant
+      for (int q = 0; q < 9; ++q) B[q] = A[q];
+      continue;
+    }
+    double T[3][3];
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) {
+        T[i][j] = 0.0;
+        for (int p = 0; p < 3; ++p)
+          for (int q = 0; q < 3; ++q) T[i][j] += Rm[i][p] * A[3 * p + q] * Rm[j][q];
+      }
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) B[3 * i + j] = 0.5 * (T[i][j] + T[j][i]);
+  }
+  return rp_create(h.n_nuc, h.radical.data(), h.two_I.data(), A2.data(), h.k_S, h.k_T, h.J_mT, out);
+}
+
 rp_status rp_create(int n_nuc, const int* radical, const int* two_I, const double* A, double k_S,
                     double k_T, double J, rp_system** out) {
   g_err.clear();
@@ -1573,6 +1645,50 @@ rp_status rp_time_trace(rp_system* s, double B, int M, uint64_t seed, double t_m
     if (ds != RP_OK) return ds;
     if (o.precision == RP_FP64) return run_time_trace<double>(s, B, M, seed, t_max, o, nt, t, out);
     return run_time_trace<float>(s, B, M, seed, t_max, o, nt, t, out);
+  } catch (const CudaFail& e) {
+    return fail(e.st, e.msg);
+  } catch (const std::bad_alloc&) {
+    return fail(RP_ENOMEM, "host allocation failed");
+  }
+}
+
+rp_status rp_time_observable(rp_system* s, double B, int M, uint64_t seed, double t_max,
+                             const rp_options* opt, const double* A, int max_times,
+                             int* n_times, double* t, double* out) {
+  g_err.clear();
+  if (!A) return fail(RP_EINVAL, "A is NULL");
+  for (int q = 0; q < 32; ++q)
+    if (!std::isfinite(A[q])) return fail(RP_EINVAL, "non-finite operator entry");
+  rp_options o;
+  if (opt) o = *opt;
+  else rp_default_options(&o);
+  if (!s || !n_times) return fail(RP_EINVAL, "system or n_times is NULL");
+  if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
+  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..4, gram 0..2 and graph 0 or 1");
+  if (o.deterministic == 3) return fail(RP_ENOTIMPL, "rp_time_observable does not take the J_z-sector trace (deterministic = 3)");
+  if (o.deterministic < 0 || o.deterministic > 2) return fail(RP_EINVAL, "deterministic must be 0, 1 or 2");
+  if (o.deterministic != 1 && M < 1) return fail(RP_EINVAL, "M must be >= 1");
+  if (!(t_max > 0.0) || !std::isfinite(t_max)) return fail(RP_EINVAL, "t_max must be positive and finite");
+  if (!std::isfinite(B)) return fail(RP_EINVAL, "non-finite field");
+  if (o.sample_offset < 0) return fail(RP_EINVAL, "sample_offset must be >= 0");
+  const int n_c = o.n_cheb > 0 ? o.n_cheb : default_ncheb(o.precision);
+  if (n_c % 4 != 0 || n_c < 8 || n_c > 88)
+    return fail(RP_EINVAL, "n_cheb must be a multiple of 4 in [8, 88]");
+  try {
+    std::vector<rp::FieldPlan> plans;
+    rp_status ps = plan_all(s->hs, 1, &B, t_max, n_c, o.tol > 0 ? o.tol : default_tol(o.precision),
+                            plans);
+    if (ps != RP_OK) return ps;
+    if (plans[0].n_macro + 1 > (long long)INT32_MAX) return fail(RP_EINVAL, "too many time points");
+    const int nt = (int)(plans[0].n_macro + 1);
+    *n_times = nt;
+    if (!t || !out) return RP_OK;  // size query
+    if (max_times < nt) return fail(RP_EINVAL, "max_times is smaller than the number of time points");
+    rp_status ds = check_device();
+    if (ds != RP_OK) return ds;
+    if (o.precision == RP_FP64)
+      return run_time_trace<double>(s, B, M, seed, t_max, o, nt, t, nullptr, A, out);
+    return run_time_trace<float>(s, B, M, seed, t_max, o, nt, t, nullptr, A, out);
   } catch (const CudaFail& e) {
     return fail(e.st, e.msg);
   } catch (const std::bad_alloc&) {

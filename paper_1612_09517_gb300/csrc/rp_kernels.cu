@@ -1383,15 +1383,17 @@ __global__ void __launch_bounds__(kGramThreads) k_gram_integrate(
   if (tid == 0) atomicAdd(integral + r, tot);
 }
 
-// Time-resolved observables (Eq. 18 for A = P_S and A = 1): after macro-step
-// k, every row active in it holds psi(t_i), i = k + 1 - start, in Q; adds
-// |<S|psi>|^2 (P_S = |S><S| on the electrons, identity on the nuclei) and
-// |psi|^2 over a slice of its configurations into trace[2 i] and
-// trace[2 i + 1] (FP64, summed over rows).
+// Time-resolved observables (Eq. 18 for A = P_S, A = 1 and an electron
+// operator A_e): after macro-step k, every row active in it holds psi(t_i),
+// i = k + 1 - start, in Q; adds |<S|psi>|^2 (P_S = |S><S| on the electrons,
+// identity on the nuclei), |psi|^2 and <psi| A_e x 1 |psi> over a slice of its
+// configurations into trace[4 i .. 4 i + 3] (P_S, norm, Re, Im; FP64, summed
+// over rows).
 template <typename T>
 __global__ void __launch_bounds__(256) k_trace(const SysTab<T> ST, const T* __restrict__ Q,
                                                const int2* __restrict__ row_win, int macro,
-                                               long long z_per_cta, double* __restrict__ trace) {
+                                               long long z_per_cta, ElecOp A,
+                                               double* __restrict__ trace) {
   __shared__ double sh[256];
   const int r = blockIdx.y;
   const int2 w = row_win[r];
@@ -1400,7 +1402,7 @@ __global__ void __launch_bounds__(256) k_trace(const SysTab<T> ST, const T* __re
   const T* S = Q + (size_t)r * ST.Zslot * 8;
   const long long z0 = (long long)blockIdx.x * z_per_cta;
   const long long z1 = min(Z, z0 + z_per_cta);
-  double ps = 0.0, nn = 0.0;
+  double ps = 0.0, nn = 0.0, ar = 0.0, ai = 0.0;
   for (long long m = z0 + threadIdx.x; m < z1; m += blockDim.x) {
     Cx<T> a[4];
     load4(S + m * 8, a);
@@ -1409,13 +1411,37 @@ __global__ void __launch_bounds__(256) k_trace(const SysTab<T> ST, const T* __re
 #pragma unroll
     for (int e = 0; e < 4; ++e)
       nn += (double)a[e].re * (double)a[e].re + (double)a[e].im * (double)a[e].im;
+    if (A.on) {
+      // sum_e conj(a_e) (A a)_e
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        double yr = 0.0, yi = 0.0;
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+          const double xr = (double)a[f].re, xi = (double)a[f].im;
+          yr += A.re[4 * e + f] * xr - A.im[4 * e + f] * xi;
+          yi += A.re[4 * e + f] * xi + A.im[4 * e + f] * xr;
+        }
+        const double cr = (double)a[e].re, ci = (double)a[e].im;
+        ar += cr * yr + ci * yi;
+        ai += cr * yi - ci * yr;
+      }
+    }
   }
   const int i = macro + 1 - w.x;
   const double tps = block_sum<256>(ps, sh);
-  if (threadIdx.x == 0) atomicAdd(trace + 2 * i, tps);
+  if (threadIdx.x == 0) atomicAdd(trace + 4 * i, tps);
   __syncthreads();
   const double tnn = block_sum<256>(nn, sh);
-  if (threadIdx.x == 0) atomicAdd(trace + 2 * i + 1, tnn);
+  if (threadIdx.x == 0) atomicAdd(trace + 4 * i + 1, tnn);
+  if (A.on) {
+    __syncthreads();
+    const double tar = block_sum<256>(ar, sh);
+    if (threadIdx.x == 0) atomicAdd(trace + 4 * i + 2, tar);
+    __syncthreads();
+    const double tai = block_sum<256>(ai, sh);
+    if (threadIdx.x == 0) atomicAdd(trace + 4 * i + 3, tai);
+  }
 }
 
 // survival[r] += |psi|^2 over a slice for the flagged rows; psi of a row whose
@@ -1987,11 +2013,11 @@ size_t xblk_floats_per_row(long long Zs, int n_c) { return xblk_row_floats(Zs, n
 
 template <typename T>
 cudaError_t launch_trace(const SysTab<T>& S, const T* Q, const int2* row_win, int macro, int rows,
-                         double* trace, cudaStream_t st) {
+                         const ElecOp& A, double* trace, cudaStream_t st) {
   if (rows == 0) return cudaSuccess;
   const long long zper = 8192;
   dim3 grid(grid1(S.Zslot, (int)zper), rows);
-  k_trace<T><<<grid, 256, 0, st>>>(S, Q, row_win, macro, zper, trace);
+  k_trace<T><<<grid, 256, 0, st>>>(S, Q, row_win, macro, zper, A, trace);
   return cudaGetLastError();
 }
 
@@ -2026,7 +2052,7 @@ template cudaError_t launch_macro_small<float>(const SysTab<float>&, const HamDe
 template cudaError_t launch_norm<float>(const SysTab<float>&, const float*, const float*, const int2*,
                                         const int*, int, double*, cudaStream_t);
 template cudaError_t launch_trace<float>(const SysTab<float>&, const float*, const int2*, int, int,
-                                         double*, cudaStream_t);
+                                         const ElecOp&, double*, cudaStream_t);
 template cudaError_t launch_finalize<float>(const SysTab<float>&, const RowsDev&, int, double*,
                                             cudaStream_t);
 template cudaError_t launch_coherent_amps<double>(const SysTab<double>&, const long long*, const int*,
@@ -2049,7 +2075,7 @@ template cudaError_t launch_macro_small<double>(const SysTab<double>&, const Ham
 template cudaError_t launch_norm<double>(const SysTab<double>&, const double*, const double*, const int2*,
                                         const int*, int, double*, cudaStream_t);
 template cudaError_t launch_trace<double>(const SysTab<double>&, const double*, const int2*, int, int,
-                                         double*, cudaStream_t);
+                                         const ElecOp&, double*, cudaStream_t);
 template cudaError_t launch_finalize<double>(const SysTab<double>&, const RowsDev&, int, double*,
                                             cudaStream_t);
 

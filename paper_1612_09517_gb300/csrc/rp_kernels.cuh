@@ -190,11 +190,19 @@ size_t xblk_floats_per_row(long long Zs, int n_c);
 // *macro_dev += 1 (one thread): ends a graph-replayed macro-step.
 cudaError_t launch_tick(int* macro_dev, cudaStream_t st);
 
-// After macro-step `macro`: trace[2 i] += |<S|psi>|^2, trace[2 i + 1] += |psi|^2
-// for every row active in it, psi = psi(t_i) in Q, i = macro + 1 - start.
+// A 4 x 4 complex operator on the electron states e = 2 e1 + e2 (row-major),
+// applied as A x 1 on the nuclei; on = 0 switches it off.
+struct ElecOp {
+  double re[16], im[16];
+  int on;
+};
+
+// After macro-step `macro`, for every row active in it (psi = psi(t_i) in Q,
+// i = macro + 1 - start): trace[4 i] += |<S|psi>|^2, trace[4 i + 1] += |psi|^2,
+// and if A.on trace[4 i + 2] + i trace[4 i + 3] += <psi| A x 1 |psi>.
 template <typename T>
 cudaError_t launch_trace(const SysTab<T>& S, const T* Q, const int2* row_win, int macro, int rows,
-                         double* trace, cudaStream_t st);
+                         const ElecOp& A, double* trace, cudaStream_t st);
 
 template <typename T>
 cudaError_t launch_norm(const SysTab<T>& S, const T* S0, const T* S1, const int2* row_win,

@@ -144,6 +144,11 @@ SIGNATURES = [
     ("rp_basis_indices", C.c_int, [C.c_uint64, C.c_uint32, C.c_longlong, C.c_int, C.c_longlong,
                                    C.POINTER(C.c_longlong)]),
     ("rp_trace_propagations", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_longlong)]),
+    ("rp_rotate", C.c_int, [C.c_void_p, C.c_double, C.c_double, C.POINTER(C.c_void_p)]),
+    ("rp_time_observable", C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_uint64, C.c_double,
+                                     C.POINTER(rp_options), C.POINTER(C.c_double), C.c_int,
+                                     C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double)]),
     ("rp_time_trace", C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_uint64, C.c_double,
                                 C.POINTER(rp_options), C.c_int, C.POINTER(C.c_int),
                                 C.POINTER(C.c_double), C.POINTER(C.c_double)]),
@@ -306,6 +311,23 @@ def rp_time_trace(h, B, M, seed, t_max, opt=None):
     return t, out.reshape(-1, 3)
 
 
+def rp_time_observable(h, B, M, seed, t_max, A_e, opt=None):
+    """Sample mean of <psi(t)| A_e x 1 |psi(t)> at the macro-step boundaries for a
+    4 x 4 complex electron operator A_e: returns (t, values complex array)."""
+    o = opt if opt is not None else rp_default_options()
+    A = np.zeros(32)
+    A[0::2] = np.real(np.asarray(A_e, complex)).ravel()
+    A[1::2] = np.imag(np.asarray(A_e, complex)).ravel()
+    n = C.c_int(0)
+    _check(LIB.rp_time_observable(h, float(B), int(M), C.c_uint64(int(seed)), float(t_max),
+                                  C.byref(o), _dptr(A), 0, C.byref(n), None, None))
+    t = np.zeros(n.value)
+    out = np.zeros(2 * n.value)
+    _check(LIB.rp_time_observable(h, float(B), int(M), C.c_uint64(int(seed)), float(t_max),
+                                  C.byref(o), _dptr(A), n.value, C.byref(n), _dptr(t), _dptr(out)))
+    return t, out[0::2] + 1j * out[1::2]
+
+
 def rp_tune(h, B, rows, opt=None):
     """Measured choice of kernel path, n_cheb and graph replay for `rows`
     concurrent samples at field B; returns (tuned rp_options, result dict)."""
@@ -360,6 +382,18 @@ class System:
         self.n_nuc = int(np.asarray(s.radical).size)
         self.handle = rp_create(s.radical, s.two_I, s.A, s.k_S, s.k_T, s.J)
         self.order, self.Z = rp_layout(self.handle, self.n_nuc)
+
+    @classmethod
+    def rotated(cls, system, theta, phi):
+        """rp_rotate: the same pair with the field along n(theta, phi)."""
+        h = C.c_void_p()
+        _check(LIB.rp_rotate(system.handle, float(theta), float(phi), C.byref(h)))
+        obj = cls.__new__(cls)
+        obj.spin_system = system.spin_system
+        obj.n_nuc = system.n_nuc
+        obj.handle = h
+        obj.order, obj.Z = rp_layout(h, obj.n_nuc)
+        return obj
 
     def close(self):
         if self.handle:

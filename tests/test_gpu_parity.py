@@ -616,3 +616,81 @@ def test_basis_state_sampling_matches_oracle(prec):
     assert np.allclose(np.abs(psi0 @ coherent.basis_states(s).conj().T).max(axis=1), 1.0)
     phS, phT, surv = dense.sample_yields(s, B, T, psi0)
     _cmp_per_sample(r["per_sample"][0], phS, phT, surv, prec)
+
+
+# ------------------------------------------------ field direction (rp_rotate)
+
+def _rot_to_z(theta, phi):
+    """R_y(-theta) R_z(-phi), the rotation taking n(theta, phi) to z."""
+    ct, st, cp, sp = math.cos(theta), math.sin(theta), math.cos(phi), math.sin(phi)
+    Rz = np.array([[cp, sp, 0.0], [-sp, cp, 0.0], [0.0, 0.0, 1.0]])
+    Ry = np.array([[ct, 0.0, -st], [0.0, 1.0, 0.0], [st, 0.0, ct]])
+    return Ry @ Rz
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_field_direction_matches_oracle(prec):
+    """A field along n(theta, phi) for an anisotropic pair (rp_rotate): the
+    deterministic trace equals the oracle's with the Zeeman term omega n.S
+    (Eq. 1), and each coherent-state sample equals the oracle's lab-frame
+    sample whose directions are R^T n_k."""
+    rp = _rp()
+    s = wl.random_anisotropic(2, 1, two_I=[1, 2, 1], k_S=2.0, k_T=0.5, J=0.3, seed=40)
+    sy = rp.System(s)
+    th, ph = 0.7, 1.9
+    n = np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+    sr = rp.System.rotated(sy, th, ph)
+    fields = np.array([0.5, 2.0])
+    T = 2.0
+    tr = sr.yields(fields, 2, 0, T, precision=prec, deterministic=1)
+    for i, B in enumerate(fields):
+        ref = dense.trace_yields(s, B, T, direction=n)
+        assert abs(tr["out"][i, 0] - ref[0]) < TOL[prec] * abs(ref[0])
+    r = sr.yields(fields, 5, 9, T, per_sample=True, precision=prec)
+    th_k, ph_k = philox.draw_angles(9, 0, np.arange(5), s.n_nuc)
+    R = _rot_to_z(th, ph)
+    psi0 = []
+    for i in range(5):
+        nk = np.stack([np.sin(th_k[i]) * np.cos(ph_k[i]), np.sin(th_k[i]) * np.sin(ph_k[i]),
+                       np.cos(th_k[i])], -1) @ R  # rows: R^T n_k
+        lt = np.arccos(np.clip(nk[:, 2], -1, 1))
+        lp = np.arctan2(nk[:, 1], nk[:, 0])
+        psi0.append(coherent.sample_state(s, lt, lp))
+    for i, B in enumerate(fields):
+        phS, phT, surv = dense.sample_yields(s, B, T, np.array(psi0), direction=n)
+        _cmp_per_sample(r["per_sample"][i], phS, phT, surv, prec)
+
+
+# ------------------------------------------ time-resolved electron observables
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_time_observable_matches_oracle(prec):
+    """rp_time_observable: <psi(t)| A_e x 1 |psi(t)> averaged over samples at
+    the macro-step boundaries (Eq. 18 with a general electron operator)
+    against the oracle's dense propagation, for S_1z, S_1x S_2y + h.c. and the
+    triplet projector T_0; A_e = P_S reproduces rp_time_trace."""
+    rp = _rp()
+    s = wl.random_isotropic(2, 1, two_I=[1, 2, 1], k_S=2.0, k_T=0.5, J=0.3, seed=45)
+    sy = rp.System(s)
+    B, M, T = 1.7, 4, 0.6
+    sx = np.array([[0, 0.5], [0.5, 0]], complex)
+    sy_ = np.array([[0, -0.5j], [0.5j, 0]])
+    sz = np.diag([0.5, -0.5]).astype(complex)
+    e2 = np.eye(2)
+    t0 = np.zeros((4, 4), complex)
+    v = np.array([0, 1, 1, 0]) / math.sqrt(2)
+    t0 = np.outer(v, v).astype(complex)
+    singlet = np.array([0, 1, -1, 0]) / math.sqrt(2)
+    ops_e = {"S1z": np.kron(sz, e2), "mix": np.kron(sx, sy_) + np.kron(sy_, sx).conj().T,
+             "T0": t0, "PS": np.outer(singlet, singlet).astype(complex)}
+    o = rp.rp_default_options(precision=prec)
+    psi0 = coherent.sample_states(s, 6, range(M))
+    Z = s.Z
+    tol = 1e-10 if prec == "fp64" else 1e-5
+    for name, Ae in ops_e.items():
+        t, val = rp.rp_time_observable(sy.handle, B, M, 6, T, Ae, o)
+        ref = dense.expectation_traces(s, B, psi0, t, [np.kron(Ae, np.eye(Z))])[:, 0]
+        assert np.max(np.abs(val - ref)) < tol, (name, np.max(np.abs(val - ref)))
+    t2, tr = rp.rp_time_trace(sy.handle, B, M, 6, T, o)
+    _, ps = rp.rp_time_observable(sy.handle, B, M, 6, T, ops_e["PS"], o)
+    assert np.allclose(t2, t) and np.max(np.abs(ps.real - tr[:, 0])) < 1e-12

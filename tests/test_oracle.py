@@ -432,3 +432,60 @@ def test_basis_index_draw_is_uniform_and_disjoint_from_angles():
     assert chi2 < 100.0  # 47 dof: P(chi2 > 100) < 1e-5
     u1, _ = philox.draw_uniforms(5, 3, np.arange(8), 1)
     assert not np.array_equal(np.floor(u1[:, 0] * Z).astype(np.int64), idx[:8])
+
+
+# ------------------------------------------- field direction, general observables
+
+def _rot_to_z(theta, phi):
+    """R_y(-theta) R_z(-phi): the rotation taking n(theta, phi) to z."""
+    ct, st, cp, sp = math.cos(theta), math.sin(theta), math.cos(phi), math.sin(phi)
+    Rz = np.array([[cp, sp, 0.0], [-sp, cp, 0.0], [0.0, 0.0, 1.0]])
+    Ry = np.array([[ct, 0.0, -st], [0.0, 1.0, 0.0], [st, 0.0, ct]])
+    return Ry @ Rz
+
+
+def test_field_direction_hamiltonian():
+    """Eq. 1 with omega = |gamma_e| B n: n = z gives the z Hamiltonian exactly;
+    an isotropic system's trace does not depend on the direction (a global
+    rotation of every spin leaves P_S / Z invariant); an anisotropic system
+    with the field along n has the trace of the system with tensors R A R^T
+    and the field along z (R n = z)."""
+    s = wl.random_anisotropic(2, 1, two_I=[1, 2, 1], k_S=2.0, k_T=0.5, J=0.3, seed=40)
+    assert np.array_equal(spin.hamiltonian(s, 1.3), spin.hamiltonian(s, 1.3, [0, 0, 1]))
+    th, ph = 0.7, 1.9
+    n = np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+    R = _rot_to_z(th, ph)
+    assert np.allclose(R @ n, [0, 0, 1], atol=1e-15)
+    iso = wl.random_isotropic(2, 1, two_I=[1, 2, 1], k_S=2.0, k_T=0.5, J=0.3, seed=40)
+    a = dense.trace_yields(iso, 1.5, 2.0)
+    b = dense.trace_yields(iso, 1.5, 2.0, direction=n)
+    assert np.allclose(a, b, rtol=1e-11, atol=1e-13)
+    rot = wl.SpinSystem(s.radical, s.two_I, np.einsum("ij,kjl,ml->kim", R, s.A, R), s.k_S, s.k_T,
+                        s.J)
+    a = dense.trace_yields(s, 1.5, 2.0, direction=n)
+    b = dense.trace_yields(rot, 1.5, 2.0)
+    assert np.allclose(a, b, rtol=1e-11, atol=1e-13)
+    # and the direction matters for the anisotropic system
+    assert abs(a[0] - dense.trace_yields(s, 1.5, 2.0)[0]) > 1e-4
+
+
+def test_expectation_traces_closed_forms():
+    """<P_S>(t) = e^{-kt}(5/8 + 3/8 cos at) and <1>(t) = e^{-kt} for one
+    spin-1/2 nucleus at zero field with k_S = k_T = k; <S_1z>(t) = 0 at zero
+    field (the singlet and the isotropic coupling are rotation invariant)."""
+    a_mT, k = 1.0, 1.0
+    s = wl.one_nucleus(a_mT, 1, k)
+    a = spin.GAMMA_E * a_mT
+    PS, _ = spin.projectors(s)
+    S1, _ = spin.electron_ops(s)
+    psi0 = coherent.sample_states(s, 3, range(6))
+    times = np.array([0.0, 0.013, 0.2, 1.1])
+    out = dense.expectation_traces(s, 0.0, psi0, times, [PS, np.eye(PS.shape[0]), S1[2]])
+    for i, t in enumerate(times):
+        assert abs(out[i, 0] - math.exp(-k * t) * (5 / 8 + 3 / 8 * math.cos(a * t))) < 1e-10
+        assert abs(out[i, 1] - math.exp(-k * t)) < 1e-12
+    assert np.max(np.abs(out[:, 0].imag)) < 1e-14
+    # a single sample has <S_1z> != 0 in general; the mean over the sphere is 0
+    full = coherent.sample_states(s, 3, range(4000))
+    m = dense.expectation_traces(s, 0.0, full, [0.2], [S1[2]])
+    assert abs(m[0, 0]) < 5e-3
