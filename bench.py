@@ -253,8 +253,9 @@ def parse():
                          "to check its bias; prints one JSON line")
     ap.add_argument("--table1", action="store_true",
                     help="the paper's model problem (Table I couplings, Z = 2^20): Phi_S(B) at 21 "
-                         "fields 0-10 mT with M = 200 (and the first 100 samples), the field of "
-                         "the minimum, per-sample histograms at three fields; one JSON line")
+                         "fields 0-10 mT with M = 400 (and the first 100 and 200 samples, as in "
+                         "Fig. 2), the field of the minimum, per-sample histograms at three "
+                         "fields (Fig. 4); one JSON line")
     ap.add_argument("--basis-sampling", action="store_true",
                     help="config-2 system, 3 fields x 200 samples: spread of phi_S with "
                          "coherent-state samples vs random basis states (deterministic = 2); "
@@ -423,17 +424,24 @@ def main():
         sy1 = rp.System(s1)
         T1 = 10.0 / min(s1.k_S, s1.k_T)  # survival e^-10 at the horizon
         B1 = np.linspace(0.0, 10.0, 21)
+        M1 = 400
         o = rp.rp_default_options(precision=prec, stream=torch.cuda.current_stream().cuda_stream)
         t0 = time.perf_counter()
-        r = rp.rp_yields(sy1.handle, B1, 200, 0, T1, o, per_sample=True)
+        r = rp.rp_yields(sy1.handle, B1, M1, 0, T1, o, per_sample=True)
         wall = time.perf_counter() - t0
         ps = r["per_sample"][:, :, 0]
         curve = {}
-        for M in (100, 200):
+        for M in (100, 200, 400):
             x = ps[:, :M]
             mean, se = x.mean(1), x.std(1, ddof=1) / np.sqrt(M)
             curve[M] = {"PhiS": mean.round(6).tolist(), "SE": se.round(6).tolist(),
                         "B_min_mT": float(B1[int(np.argmin(mean))])}
+        # Fig. 2: the M = 100 and M = 200 curves against the M = 400 curve, in
+        # units of their own error bars (the samples are nested, so this is a
+        # consistency check, not an independent test)
+        ref = np.array(curve[400]["PhiS"])
+        dev = {M: (np.abs(np.array(curve[M]["PhiS"]) - ref) / np.array(curve[M]["SE"])).round(3).tolist()
+               for M in (100, 200)}
         hist = {}
         for b in (0.0, 3.5, 10.0):
             j = int(np.argmin(np.abs(B1 - b)))
@@ -442,10 +450,11 @@ def main():
                             "sd": float(ps[j].std(ddof=1)), "min": float(ps[j].min()),
                             "max": float(ps[j].max())}
         print(json.dumps({"mode": "table1", "Z": int(s1.Z), "t_max_us": T1, "fields_mT": B1.tolist(),
-                          "two_J_over_gamma_mT": 2 * s1.J, "wall_s": wall,
+                          "two_J_over_gamma_mT": 2 * s1.J, "M": M1, "wall_s": wall,
                           "device_ms": r["stats"]["device_ms"], "row_terms": r["stats"]["row_terms"],
                           "mean_survival": float(r["out"][:, 4].max()),
-                          "M100": curve[100], "M200": curve[200], "hist": hist}), flush=True)
+                          "M100": curve[100], "M200": curve[200], "M400": curve[400],
+                          "deviation_from_M400_in_SE": dev, "hist": hist}), flush=True)
         return
     if args.trace:
         fb = w.fields[[2, 4]]
