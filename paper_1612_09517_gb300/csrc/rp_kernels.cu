@@ -1024,7 +1024,9 @@ struct ClusterShape {
   static constexpr unsigned kZl = kStatic ? (1u << (LB < 0 ? 0 : LB)) * pow3(N1 < 0 ? 0 : N1) : 0u;
 };
 
-template <int LB, int CB, int N1, int KPT>
+// RR >= 0: the radical bit masks known at compile time, packed as
+// rr_in | rr_out << 12 | rr_one << 15 (else read from ClusterConst).
+template <int LB, int CB, int N1, int KPT, int RR = -1>
 __global__ void __launch_bounds__(ClusterCfg<KPT>::kNT, 1) k_macro_cluster(
     const ClusterConst K, const HamDev<float> H, const FieldDev<float>* __restrict__ fields,
     const int* __restrict__ row_field, const int2* __restrict__ row_win, int macro_arg,
@@ -1107,7 +1109,7 @@ __global__ void __launch_bounds__(ClusterCfg<KPT>::kNT, 1) k_macro_cluster(
       for (int i = 0; i < (Sh::kStatic ? CB : kClusterMaxBits); ++i) {
         if (Sh::kStatic || i < cbits) {
           const unsigned pc = sbase + (bo + l) * 8u, peer = rank ^ (1u << i);
-          const unsigned rr = (K.rr_out >> i) & 1u;
+          const unsigned rr = ((RR >= 0 ? ((unsigned)RR >> 12) & 7u : K.rr_out) >> i) & 1u;
           const float g = K.g_out[i];
           if ((rank >> i) & 1u) {
             flip_add<false>(y, rr, g, ld_peer(pc + flip_p0<false>(rr) * Zl * 8u, peer),
@@ -1128,7 +1130,7 @@ __global__ void __launch_bounds__(ClusterCfg<KPT>::kNT, 1) k_macro_cluster(
         if (Sh::kStatic || p < lb) {
           const unsigned jb = (l >> p) & 1u;
           const float2* q8 = cur + (l ^ (1u << p));
-          const unsigned rr = (K.rr_in >> p) & 1u;
+          const unsigned rr = ((RR >= 0 ? (unsigned)RR & 0xFFFu : K.rr_in) >> p) & 1u;
           const float g = K.g_in[p];
           const float gu = jb ? 0.f : g, gd = jb ? g : 0.f;
           const float dz = jb ? -g : g;
@@ -1160,7 +1162,7 @@ __global__ void __launch_bounds__(ClusterCfg<KPT>::kNT, 1) k_macro_cluster(
         if (Sh::kStatic || i < n_one) {
           const unsigned jd = qd % 3u;
           qd /= 3u;
-          const unsigned rr = (K.rr_one >> i) & 1u;
+          const unsigned rr = ((RR >= 0 ? ((unsigned)RR >> 15) & 0xFFu : K.rr_one) >> i) & 1u;
           const float g = K.g_one[i];
           const float dz = (1.f - (float)jd) * K.v_one[i];
           if (rr == 0u) bz1 += dz;
@@ -1858,13 +1860,13 @@ ClusterConst cluster_const(const HamDev<float>& H, const ClusterPlan& cp) {
   return K;
 }
 
-template <int LB, int CB, int N1, int KPT>
+template <int LB, int CB, int N1, int KPT, int RR = -1>
 cudaError_t cluster_attr(std::atomic<unsigned long long>& done) {
   // the largest dynamic shared memory any launch of this instance asks for
-  return smem_attr_once((const void*)k_macro_cluster<LB, CB, N1, KPT>, 232448 - 1024, done);
+  return smem_attr_once((const void*)k_macro_cluster<LB, CB, N1, KPT, RR>, 232448 - 1024, done);
 }
 
-std::atomic<unsigned long long> g_cluster_attr[4];
+std::atomic<unsigned long long> g_cluster_attr[5];
 
 cudaLaunchConfig_t cluster_cfg(const ClusterPlan& cp, int rows, cudaStream_t st,
                                cudaLaunchAttribute* at) {
@@ -1885,8 +1887,14 @@ cudaLaunchConfig_t cluster_cfg(const ClusterPlan& cp, int rows, cudaStream_t st,
 // Instance of a plan: 3 for the compiled shape (5 inner spin-1/2 nuclei, 8
 // CTAs, 4 spin-1 nuclei: the 12-nucleus workload with Z = 20736), else the
 // generic instance of its configurations per thread (0, 1, 2).
+constexpr int kRR534 = 0 | (7 << 12) | (12 << 15);  // radicals of the compiled 5/3/4 instance
+
 int cluster_instance(const ClusterPlan& cp, const HamDev<float>& H) {
-  if (H.n_half - cp.cbits == 5 && cp.cbits == 3 && H.n_one == 4 && cp.kpt == 3) return 3;
+  if (H.n_half - cp.cbits == 5 && cp.cbits == 3 && H.n_one == 4 && cp.kpt == 3) {
+    const ClusterConst K = cluster_const(H, cp);
+    const int rr = (int)(K.rr_in | (K.rr_out << 12) | (K.rr_one << 15));
+    return rr == kRR534 ? 4 : 3;
+  }
   return cp.kpt - 1;
 }
 
@@ -1909,20 +1917,27 @@ cudaError_t launch_macro_cluster(const HamDev<float>& H, const FieldDev<float>* 
   if (e == cudaSuccess)                                                                            \
     e = cudaLaunchKernelEx(&cfg, k_macro_cluster<LB_, CB_, N1_, KPT_>, K, H, fields, row_field,   \
                            row_win, macro, macro_dev, P, Q, X, coef, n_c, Zslot, xblk);
+#define RP_CL2(LB_, CB_, N1_, KPT_, RR_, I_)                                                      \
+  e = cluster_attr<LB_, CB_, N1_, KPT_, RR_>(g_cluster_attr[I_]);                                 \
+  if (e == cudaSuccess)                                                                            \
+    e = cudaLaunchKernelEx(&cfg, k_macro_cluster<LB_, CB_, N1_, KPT_, RR_>, K, H, fields,         \
+                           row_field, row_win, macro, macro_dev, P, Q, X, coef, n_c, Zslot, xblk);
   switch (cluster_instance(cp, H)) {
     case 0: RP_CL(-1, -1, -1, 1, 0) break;
     case 1: RP_CL(-1, -1, -1, 2, 1) break;
     case 2: RP_CL(-1, -1, -1, 3, 2) break;
-    default: RP_CL(5, 3, 4, 3, 3) break;
+    case 3: RP_CL(5, 3, 4, 3, 3) break;
+    default: RP_CL2(5, 3, 4, 3, kRR534, 4) break;
   }
 #undef RP_CL
+#undef RP_CL2
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 bool macro_cluster_default(const HamDev<float>& H) {
   ClusterPlan cp;
-  return macro_cluster_plan(H, &cp) && cluster_instance(cp, H) == 3;
+  return macro_cluster_plan(H, &cp) && cluster_instance(cp, H) >= 3;
 }
 
 int macro_cluster_max_active(const HamDev<float>& H) {
@@ -1935,13 +1950,19 @@ int macro_cluster_max_active(const HamDev<float>& H) {
 #define RP_CL(LB_, CB_, N1_, KPT_, I_)                                                            \
   e = cluster_attr<LB_, CB_, N1_, KPT_>(g_cluster_attr[I_]);                                      \
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveClusters(&n, k_macro_cluster<LB_, CB_, N1_, KPT_>, &cfg);
+#define RP_CL2(LB_, CB_, N1_, KPT_, RR_, I_)                                                      \
+  e = cluster_attr<LB_, CB_, N1_, KPT_, RR_>(g_cluster_attr[I_]);                                 \
+  if (e == cudaSuccess)                                                                            \
+    e = cudaOccupancyMaxActiveClusters(&n, k_macro_cluster<LB_, CB_, N1_, KPT_, RR_>, &cfg);
   switch (cluster_instance(cp, H)) {
     case 0: RP_CL(-1, -1, -1, 1, 0) break;
     case 1: RP_CL(-1, -1, -1, 2, 1) break;
     case 2: RP_CL(-1, -1, -1, 3, 2) break;
-    default: RP_CL(5, 3, 4, 3, 3) break;
+    case 3: RP_CL(5, 3, 4, 3, 3) break;
+    default: RP_CL2(5, 3, 4, 3, kRR534, 4) break;
   }
 #undef RP_CL
+#undef RP_CL2
   if (e != cudaSuccess) {
     cudaGetLastError();
     return 0;
