@@ -239,10 +239,12 @@ class YieldEngine {
   void set_fields(const std::vector<rp::FieldPlan>& plans) {
     const int nf = (int)plans.size();
     d_fdev_ = ar_.get<rp::FieldDev<T>>(nf);
-    d_coef_ = ar_.get<T>((size_t)nf * n_c_ * 2);
+    d_coef_ = ar_.get<T>((size_t)nf * n_c_ * 4);
     d_W_ = ar_.get<double>((size_t)nf * n_c_ * n_c_ * 2);
     std::vector<rp::FieldDev<T>> fdev(nf);
-    std::vector<T> coef((size_t)nf * n_c_ * 2);
+    // per field: c_n (re, im) in T, then the remainder c_n - fl(c_n) (FP32
+    // only: the kernels add it, so the coefficients act with FP64 accuracy)
+    std::vector<T> coef((size_t)nf * n_c_ * 4, T(0));
     std::vector<double> W((size_t)nf * n_c_ * n_c_ * 2);
     for (int f = 0; f < nf; ++f) {
       const rp::FieldPlan& P = plans[f];
@@ -251,8 +253,14 @@ class YieldEngine {
       fdev[f].sh_re = (T)(P.E_c / P.dE);
       fdev[f].sh_im = (T)0;
       for (int n = 0; n < n_c_; ++n) {
-        coef[((size_t)f * n_c_ + n) * 2] = (T)P.coef[n].real();
-        coef[((size_t)f * n_c_ + n) * 2 + 1] = (T)P.coef[n].imag();
+        const T re = (T)P.coef[n].real(), im = (T)P.coef[n].imag();
+        T* cf = &coef[(size_t)f * n_c_ * 4];
+        cf[2 * n] = re;
+        cf[2 * n + 1] = im;
+        if (sizeof(T) == 4) {
+          cf[2 * n_c_ + 2 * n] = (T)(P.coef[n].real() - (double)re);
+          cf[2 * n_c_ + 2 * n + 1] = (T)(P.coef[n].imag() - (double)im);
+        }
       }
       for (size_t i = 0; i < (size_t)n_c_ * n_c_; ++i) {
         W[((size_t)f * n_c_ * n_c_ + i) * 2] = P.W[i].real();

@@ -339,7 +339,8 @@ __device__ __forceinline__ void term_epilogue(const HamDev<T>& H, const SysTab<T
     store4(next + off, z);
     return;
   }
-  const T* cf = coef + (size_t)f * n_c * 2;
+  const T* cf = coef + (size_t)f * n_c * 4;  // c_n, then (FP32) c_n - fl(c_n)
+  const T* cl = cf + 2 * n_c;
   const size_t Zs = (size_t)S.Zslot;
   T* xr = X + (size_t)r * n_c * Zs * 2;
   if (mode == MODE_FIRST) {
@@ -349,6 +350,10 @@ __device__ __forceinline__ void term_epilogue(const HamDev<T>& H, const SysTab<T
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       s[e] = {T(0), T(0)};
+      if (sizeof(T) == 4) {
+        cmac(s[e], cl[0], cl[1], a[e]);
+        cmac(s[e], cl[2], cl[3], z[e]);
+      }
       cmac(s[e], c0r, c0i, a[e]);
       cmac(s[e], c1r, c1i, z[e]);
     }
@@ -385,7 +390,10 @@ __device__ __forceinline__ void term_epilogue(const HamDev<T>& H, const SysTab<T
   }
   const T cr = cf[2 * n], ci = cf[2 * n + 1];
 #pragma unroll
-  for (int e = 0; e < 4; ++e) cmac(s[e], cr, ci, ph[e]);
+  for (int e = 0; e < 4; ++e) {
+    if (sizeof(T) == 4) cmac(s[e], cl[2 * n], cl[2 * n + 1], ph[e]);
+    cmac(s[e], cr, ci, ph[e]);
+  }
   store4(acc + off, s);
   if (xblk) store_singlet_blk(xblk_addr(X, r, n, m, S.Zslot, n_c), ph);
   else store_singlet(xr + ((size_t)n * Zs + m) * 2, ph);
@@ -831,6 +839,7 @@ __device__ __forceinline__ void macro_small_body(const HamDev<T>& H, const SysTa
   const size_t Zs = (size_t)S.Zslot;
   T* xr = X + (size_t)r * n_c * Zs * 2;
   const T c0r = cf[0], c0i = cf[1];
+  const T* cl = cf + 2 * n_c;  // (FP32) c_n - fl(c_n)
   for (int m = threadIdx.x; m < Z; m += blockDim.x) {
     Cx<T> a[4];
     load4(P + row0 + (size_t)m * 8, a);
@@ -839,6 +848,7 @@ __device__ __forceinline__ void macro_small_body(const HamDev<T>& H, const SysTa
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       s[e] = {T(0), T(0)};
+      if (sizeof(T) == 4) cmac(s[e], cl[0], cl[1], a[e]);
       cmac(s[e], c0r, c0i, a[e]);
     }
     tile_put(accb, Z, m, s);
@@ -868,7 +878,10 @@ __device__ __forceinline__ void macro_small_body(const HamDev<T>& H, const SysTa
       Cx<T> s[4];
       tile_get(accb, Z, m, s);
 #pragma unroll
-      for (int e = 0; e < 4; ++e) cmac(s[e], cr, ci, ph[e]);
+      for (int e = 0; e < 4; ++e) {
+        if (sizeof(T) == 4) cmac(s[e], cl[2 * n], cl[2 * n + 1], ph[e]);
+        cmac(s[e], cr, ci, ph[e]);
+      }
       tile_put(accb, Z, m, s);
       store_singlet(xr + ((size_t)n * Zs + m) * 2, ph);
       if (n < n_c - 1) tile_put(nxt, Z, m, ph);
@@ -894,7 +907,7 @@ __global__ void __launch_bounds__(256) k_macro_small(
   if (macro < w.x || macro >= w.y) return;
   const int f = row_field[r];
   const FieldDev<T> F = fields[f];
-  const T* cf = coef + (size_t)f * n_c * 2;
+  const T* cf = coef + (size_t)f * n_c * 4;
   if (MULTI) {
     __shared__ HamDev<T> Hs;
     const int sidx = S.row_sys ? S.row_sys[r] : 0;
@@ -1054,7 +1067,8 @@ __global__ void __launch_bounds__(ClusterCfg<KPT>::kNT, 1) k_macro_cluster(
   const unsigned sbase = smem_u32(cl_smem);
   const int f = row_field[r];
   const FieldDev<float> F = fields[f];
-  const float* cf = coef + (size_t)f * n_c * 2;
+  const float* cf = coef + (size_t)f * n_c * 4;
+  const float* cl = cf + 2 * n_c;  // c_n - fl(c_n)
   const float* Pr = P + (size_t)r * Zslot * 8;
   float* Qr = Q + (size_t)r * Zslot * 8;
   float* Xr = xblk ? X + (size_t)r * xblk_row_floats(Zslot, n_c) : X + (size_t)r * n_c * Zslot * 2;
@@ -1088,7 +1102,7 @@ __global__ void __launch_bounds__(ClusterCfg<KPT>::kNT, 1) k_macro_cluster(
     const unsigned bo = ((n - 1) & 1) * 4u * Zl;  // phi_{n-1} in buffer (n - 1) % 2
     const float2* cur = cl_smem + bo;
     float2* oth = cl_smem + (4u * Zl - bo);        // phi_{n-2}, then phi_n
-    const float cr = cf[2 * n], ci = cf[2 * n + 1];
+    const float cr = cf[2 * n], ci = cf[2 * n + 1], clr = cl[2 * n], cli = cl[2 * n + 1];
     // offset of slice n in a chunk (tensor-core layout) or of X[n] (plain)
     const unsigned xn = xblk ? ((2 * n) >> 3) * 128 + ((2 * n) & 7) * 4 : (unsigned)(2 * n * Zslot);
     const unsigned ximag = xblk ? 4u : 1u;
@@ -1191,6 +1205,7 @@ __global__ void __launch_bounds__(ClusterCfg<KPT>::kNT, 1) k_macro_cluster(
         for (int e = 0; e < 4; ++e) {
           ph[e] = z[e];
           s[e] = {0.f, 0.f};
+          cmac(s[e], cl[0], cl[1], a[e]);
           cmac(s[e], c0r, c0i, a[e]);
         }
         float* x0 = Xr + xj[j];
@@ -1213,7 +1228,10 @@ __global__ void __launch_bounds__(ClusterCfg<KPT>::kNT, 1) k_macro_cluster(
         }
       }
 #pragma unroll
-      for (int e = 0; e < 4; ++e) cmac(s[e], cr, ci, ph[e]);
+      for (int e = 0; e < 4; ++e) {
+        cmac(s[e], clr, cli, ph[e]);
+        cmac(s[e], cr, ci, ph[e]);
+      }
       if (j == 0) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) acc0[e] = s[e];

@@ -90,7 +90,10 @@ struct SysTab {
 };
 
 // ---- launchers (return cudaGetLastError after the launch) ----
-// row_flag may be NULL (all rows).
+// row_flag may be NULL (all rows).  coef holds 4 n_c values per field: the
+// Chebyshev coefficients c_n (re, im) in T, then in FP32 the remainders
+// c_n - fl(c_n), which the FP32 kernels add so that the coefficients act with
+// FP64 accuracy (zero and unused in FP64).
 
 template <typename T>
 cudaError_t launch_coherent_amps(const SysTab<T>& S, const long long* row_sample,

@@ -180,7 +180,7 @@ rp_status run_static(const rp::HostSystem& hs, int n_fields, const double* field
                        up256(2 * (size_t)n_fields * sizeof(long long)) +
                        up256(sizeof(rp::HamDev<T>)) + up256(sizeof(rp::LayoutDev)) + up256(sizeof(double)) +
                        up256((size_t)n_fields * sizeof(rp::FieldDev<T>)) +
-                       up256((size_t)n_fields * n_c * 2 * sizeof(T)) +
+                       up256((size_t)n_fields * n_c * 4 * sizeof(T)) +
                        up256((size_t)n_fields * n_c * n_c * 2 * sizeof(double));
   auto rows_bytes = [&](size_t R) {
     return 4 * up256(R * vec * sizeof(T)) + up256(R * n_c * Z * 2 * sizeof(T)) +
@@ -200,7 +200,7 @@ rp_status run_static(const rp::HostSystem& hs, int n_fields, const double* field
   double* d_stats = b.get<double>((size_t)n_fields * 5);
   long long* d_offcnt = b.get<long long>(2 * (size_t)n_fields);
   auto* d_fdev = b.get<rp::FieldDev<T>>(n_fields);
-  T* d_coef = b.get<T>((size_t)n_fields * n_c * 2);
+  T* d_coef = b.get<T>((size_t)n_fields * n_c * 4);
   double* d_W = b.get<double>((size_t)n_fields * n_c * n_c * 2);
   T* S0 = b.get<T>(R * vec);
   T* S1 = b.get<T>(R * vec);
@@ -216,7 +216,7 @@ rp_status run_static(const rp::HostSystem& hs, int n_fields, const double* field
   double* d_surv = d_int + R;
 
   std::vector<rp::FieldDev<T>> fdev(n_fields);
-  std::vector<T> coef((size_t)n_fields * n_c * 2);
+  std::vector<T> coef((size_t)n_fields * n_c * 4, T(0));  // c_n, then (FP32) c_n - fl(c_n)
   std::vector<double> W((size_t)n_fields * n_c * n_c * 2);
   for (int f = 0; f < n_fields; ++f) {
     const rp::FieldPlan& P = plans[f];
@@ -225,8 +225,14 @@ rp_status run_static(const rp::HostSystem& hs, int n_fields, const double* field
     fdev[f].sh_re = (T)(P.E_c / P.dE);
     fdev[f].sh_im = (T)0;
     for (int n = 0; n < n_c; ++n) {
-      coef[((size_t)f * n_c + n) * 2] = (T)P.coef[n].real();
-      coef[((size_t)f * n_c + n) * 2 + 1] = (T)P.coef[n].imag();
+      const T re = (T)P.coef[n].real(), im = (T)P.coef[n].imag();
+      T* cf = &coef[(size_t)f * n_c * 4];
+      cf[2 * n] = re;
+      cf[2 * n + 1] = im;
+      if (sizeof(T) == 4) {
+        cf[2 * n_c + 2 * n] = (T)(P.coef[n].real() - (double)re);
+        cf[2 * n_c + 2 * n + 1] = (T)(P.coef[n].imag() - (double)im);
+      }
     }
     for (size_t i = 0; i < (size_t)n_c * n_c; ++i) {
       W[((size_t)f * n_c * n_c + i) * 2] = P.W[i].real();
