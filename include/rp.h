@@ -461,6 +461,16 @@ rp_status rp_time_observable(rp_system* sys, double B, int M, uint64_t seed, dou
                              const rp_options* opt, const double* A_e, int max_times,
                              int* n_times, double* t, double* out);
 
+/* Combining estimates over disjoint sample sets (Eqs. 18, 23; host only), for
+ * sharding the samples over processes: rp_field_sums turns an rp_yields output
+ * block over M >= 2 samples (n_fields x 5: Phi_S, Phi_T, SE_S, SE_T, mean
+ * survival) into the per-field sums (sum phi_S, sum phi_S^2, sum phi_T,
+ * sum phi_T^2, sum survival), exactly up to rounding; rp_combine_sums turns
+ * sums added over sample sets with M samples in all back into an output
+ * block (M - 1 in the sample variance).  Errors: RP_EINVAL. */
+rp_status rp_field_sums(int n_fields, const double* out, long long M, double* sums);
+rp_status rp_combine_sums(int n_fields, const double* sums, long long M, double* out);
+
 /* Propagations per field of a deterministic trace (host only): Z for
  * deterministic = 1 (Eq. 14), the size of the largest class of nuclear
  * configurations with equal total M for deterministic = 3 (the J_z-sector

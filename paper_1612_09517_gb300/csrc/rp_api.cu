@@ -1601,6 +1601,44 @@ rp_status rp_basis_indices(uint64_t seed, uint32_t pair_id, long long sample_off
   return RP_OK;
 }
 
+rp_status rp_field_sums(int n_fields, const double* out, long long M, double* sums) {
+  g_err.clear();
+  if (n_fields < 0 || (n_fields > 0 && (!out || !sums))) return fail(RP_EINVAL, "bad arguments");
+  if (M < 2) return fail(RP_EINVAL, "M must be >= 2 (the standard error needs it)");
+  const double m = (double)M;
+  for (int f = 0; f < n_fields; ++f) {
+    const double* o = out + 5 * (size_t)f;
+    double* s = sums + 5 * (size_t)f;
+    // sample variance s^2 = M SE^2 (Eq. 23, M - 1), sum x^2 = (M - 1) s^2 + M mean^2
+    s[0] = m * o[0];
+    s[1] = (m - 1.0) * m * o[2] * o[2] + m * o[0] * o[0];
+    s[2] = m * o[1];
+    s[3] = (m - 1.0) * m * o[3] * o[3] + m * o[1] * o[1];
+    s[4] = m * o[4];
+  }
+  return RP_OK;
+}
+
+rp_status rp_combine_sums(int n_fields, const double* sums, long long M, double* out) {
+  g_err.clear();
+  if (n_fields < 0 || (n_fields > 0 && (!out || !sums))) return fail(RP_EINVAL, "bad arguments");
+  if (M < 2) return fail(RP_EINVAL, "M must be >= 2");
+  const double m = (double)M;
+  for (int f = 0; f < n_fields; ++f) {
+    const double* s = sums + 5 * (size_t)f;
+    double* o = out + 5 * (size_t)f;
+    const double ms = s[0] / m, mt = s[2] / m;
+    const double vs = std::max(s[1] - m * ms * ms, 0.0) / (m - 1.0);
+    const double vt = std::max(s[3] - m * mt * mt, 0.0) / (m - 1.0);
+    o[0] = ms;
+    o[1] = mt;
+    o[2] = std::sqrt(vs / m);
+    o[3] = std::sqrt(vt / m);
+    o[4] = s[4] / m;
+  }
+  return RP_OK;
+}
+
 rp_status rp_trace_propagations(const rp_system* s, int deterministic, long long* n) {
   g_err.clear();
   if (!s || !n) return fail(RP_EINVAL, "system or n is NULL");

@@ -144,6 +144,10 @@ SIGNATURES = [
     ("rp_basis_indices", C.c_int, [C.c_uint64, C.c_uint32, C.c_longlong, C.c_int, C.c_longlong,
                                    C.POINTER(C.c_longlong)]),
     ("rp_trace_propagations", C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_longlong)]),
+    ("rp_field_sums", C.c_int, [C.c_int, C.POINTER(C.c_double), C.c_longlong,
+                                C.POINTER(C.c_double)]),
+    ("rp_combine_sums", C.c_int, [C.c_int, C.POINTER(C.c_double), C.c_longlong,
+                                  C.POINTER(C.c_double)]),
     ("rp_rotate", C.c_int, [C.c_void_p, C.c_double, C.c_double, C.POINTER(C.c_void_p)]),
     ("rp_time_observable", C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_uint64, C.c_double,
                                      C.POINTER(rp_options), C.POINTER(C.c_double), C.c_int,
@@ -230,6 +234,22 @@ def rp_plan_field(h, B, t_max, precision=RP_FP64, n_cheb=0, tol=0.0, with_coef=F
         d["coef"] = coef.view(np.complex128)
         d["W"] = W.view(np.complex128).reshape(n_c, n_c)
     return d
+
+
+def rp_field_sums(out, M):
+    """Per-field sums (n_fields, 5) of an rp_yields output block over M samples."""
+    out = np.ascontiguousarray(out, dtype=np.float64).reshape(-1, 5)
+    sums = np.zeros_like(out)
+    _check(LIB.rp_field_sums(out.shape[0], _dptr(out), int(M), _dptr(sums)))
+    return sums
+
+
+def rp_combine_sums(sums, M):
+    """The rp_yields output block over M samples from summed per-field sums."""
+    sums = np.ascontiguousarray(sums, dtype=np.float64).reshape(-1, 5)
+    out = np.zeros_like(sums)
+    _check(LIB.rp_combine_sums(sums.shape[0], _dptr(sums), int(M), _dptr(out)))
+    return out
 
 
 def rp_trace_propagations(h, deterministic):

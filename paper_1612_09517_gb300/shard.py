@@ -10,12 +10,13 @@ combined with one FP64 all-reduce of five sums per field:
     sum phi_S, sum phi_S^2, sum phi_T, sum phi_T^2, sum survival,
 
 from which the global mean and standard error (Eq. 23, sample variance with
-M - 1) follow exactly.  Each rank's sums are recovered from its own
-``rp_yields`` output (mean and standard error over its M_r samples), so no
-per-sample data crosses ranks.
+M - 1) follow exactly.  Each rank's sums come from its own ``rp_yields``
+output (mean and standard error over its M_r samples) through
+``rp_field_sums``, and the combined block through ``rp_combine_sums``, both in
+the library; no per-sample data crosses ranks.
 
-Host logic only: argument marshalling around ``torch.distributed``; every
-propagation runs in the library's kernels.
+Argument marshalling around ``torch.distributed`` only; the arithmetic runs in
+the library.
 """
 from __future__ import annotations
 
@@ -37,27 +38,21 @@ def sample_range(M: int, world: int, rank: int):
 
 def field_sums(out, M: int):
     """Per-field sums (n_fields, 5) from an rp_yields output block (n_fields, 5)
-    = (Phi_S, Phi_T, SE_S, SE_T, mean survival) over M >= 2 samples."""
-    out = np.asarray(out, dtype=np.float64).reshape(-1, 5)
+    = (Phi_S, Phi_T, SE_S, SE_T, mean survival) over M >= 2 samples
+    (rp_field_sums)."""
+    from . import rp
     if M < 2:
         raise ValueError("each rank needs M >= 2 samples (the standard error needs it)")
-    m_s, m_t, se_s, se_t, surv = out.T
-    # sample variance s^2 = M SE^2, sum x^2 = (M - 1) s^2 + M mean^2
-    q_s = (M - 1) * M * se_s ** 2 + M * m_s ** 2
-    q_t = (M - 1) * M * se_t ** 2 + M * m_t ** 2
-    return np.stack([M * m_s, q_s, M * m_t, q_t, M * surv], axis=1)
+    return rp.rp_field_sums(out, M)
 
 
 def combine(sums, M: int):
-    """The rp_yields output block over all M samples from summed field_sums."""
-    sums = np.asarray(sums, dtype=np.float64).reshape(-1, 5)
+    """The rp_yields output block over all M samples from summed field_sums
+    (rp_combine_sums)."""
+    from . import rp
     if M < 2:
         raise ValueError("M must be >= 2")
-    s_s, q_s, s_t, q_t, s_u = sums.T
-    m_s, m_t = s_s / M, s_t / M
-    var_s = np.maximum(q_s - M * m_s ** 2, 0.0) / (M - 1)
-    var_t = np.maximum(q_t - M * m_t ** 2, 0.0) / (M - 1)
-    return np.stack([m_s, m_t, np.sqrt(var_s / M), np.sqrt(var_t / M), s_u / M], axis=1)
+    return rp.rp_combine_sums(sums, M)
 
 
 def allreduce_yields(out, M_local: int, group=None):
