@@ -264,6 +264,14 @@ def parse():
                     help="config 2 at 1.59 and 3.17 mT: the deterministic trace (Eq. 14) by J_z "
                          "sectors against the stochastic estimate to SE <= 1e-3, measured wall "
                          "times and the trace-level error; one JSON line")
+    ap.add_argument("--basis-aniso", action="store_true",
+                    help="config-3 system (anisotropic, Z = 2359296), 1 and 5 mT over 1 us: "
+                         "spread of phi_S with 64 coherent-state samples vs 64 random basis "
+                         "states; one JSON line")
+    ap.add_argument("--cv-size", action="store_true",
+                    help="config-2 system at 1.6 / 3.2 / 4.8 mT: variance reduction of the "
+                         "learned control variate on 1000 fresh samples per field as a function "
+                         "of the training-set size; one JSON line")
     ap.add_argument("--ncu-case3", action="store_true",
                     help="profiling case of the anisotropic config-3 system (Z = 2359296): "
                          "2 rows, two macro-steps, ~4 GB on the device")
@@ -417,6 +425,58 @@ def main():
                           [round(float(b), 4) for b in fb], "M": 200, **res,
                           "variance_ratio_basis_over_coherent": [round(x, 3) for x in ratio]}),
               flush=True)
+        return
+    if args.basis_aniso:
+        w3 = wl.config3()
+        s3 = rp.System(w3.system)
+        fb = np.array([1.0, 5.0])
+        T3, M3 = 1.0, 64
+        res = {}
+        for name, det in (("coherent", 0), ("basis", 2)):
+            o = rp.rp_default_options(precision=prec, deterministic=det,
+                                      stream=torch.cuda.current_stream().cuda_stream)
+            t0 = time.perf_counter()
+            r = rp.rp_yields(s3.handle, fb, M3, 0, T3, o, per_sample=True)
+            ps = r["per_sample"][:, :, 0]
+            res[name] = {"PhiS": ps.mean(1).round(6).tolist(),
+                         "sigma": ps.std(1, ddof=1).round(6).tolist(),
+                         "wall_s": time.perf_counter() - t0}
+        ratio = [(b / c) ** 2 for b, c in zip(res["basis"]["sigma"], res["coherent"]["sigma"])]
+        print(json.dumps({"mode": "basis-aniso", "workload": "config3 system (18x1/2 + 2x1, "
+                          "anisotropic, J = 0.1 mT, k = 1 us^-1, Z = 2359296)", "t_max_us": T3,
+                          "fields_mT": fb.tolist(), "M": M3, **res,
+                          "variance_ratio_basis_over_coherent": [round(x, 3) for x in ratio],
+                          "note": "the variance ratio carries a relative error of ~0.25 at "
+                                  "M = 64"}), flush=True)
+        return
+    if args.cv_size:
+        fb = np.array([1.6, 3.2, 4.8])
+        o = rp.rp_default_options(precision=prec, stream=torch.cuda.current_stream().cuda_stream)
+        n_max, n_test = 2400, 1000
+        t0 = time.perf_counter()
+        tr = rp.rp_yields(sy.handle, fb, n_max, 0, w.t_max, o, per_sample=True)
+        te = rp.rp_yields(sy.handle, fb, n_test, 0,
+                          w.t_max, rp.rp_default_options(precision=prec, sample_offset=1 << 30,
+                                                         stream=torch.cuda.current_stream().cuda_stream),
+                          per_sample=True)
+        t_prop = time.perf_counter() - t0
+        phi_tr, phi_te = tr["per_sample"][:, :, 0], te["per_sample"][:, :, 0]
+        res = []
+        for n in (150, 600, 2400):
+            cv = rp.ControlVariate(sy)
+            t1 = time.perf_counter()
+            cv.train(np.repeat(fb, n), np.tile(np.arange(n), len(fb)), 0, phi_tr[:, :n].ravel())
+            g = cv.eval(np.repeat(fb, n_test), np.tile(np.arange(n_test) + (1 << 30), len(fb)), 0)
+            mu, vm = cv.mean(fb, 1 << 18, 0, pair_id=1 << 30)
+            out = cv.estimate(np.arange(len(fb)) * n_test, np.full(len(fb), n_test),
+                              te["per_sample"].ravel(), g, mu, vm)
+            res.append({"train_per_field": n, "train_total": n * len(fb),
+                        "variance_reduction": [round(float(x), 3) for x in (out[:, 3] / out[:, 1]) ** 2],
+                        "beta": [round(float(x), 4) for x in out[:, 4]],
+                        "train_eval_mean_s": time.perf_counter() - t1})
+        print(json.dumps({"mode": "cv-size", "workload": WORKLOAD, "fields_mT": fb.tolist(),
+                          "test_samples_per_field": n_test, "propagation_s": t_prop,
+                          "results": res}), flush=True)
         return
     if args.table1:
         gam = 176.085963023
@@ -747,7 +807,9 @@ def _converged_runs(rp, sy, w, prec, stream):
     wall = time.perf_counter() - t0
     out["cv"] = {"wall_s": wall, "samples_plain": int(c["M_plain"].sum()),
                  "samples_cv": int(c["M_cv"].sum()), "max_SE": float(c["out"][:, 1].max()),
-                 "fields_with_cv": int(c["out"][:, 7].sum())}
+                 "fields_with_cv": int(c["out"][:, 7].sum()),
+                 "control_variate_s": c["stats"]["cv_ms"] * 1e-3,
+                 "control_variate_share": c["stats"]["cv_ms"] * 1e-3 / wall}
     out["note"] = ("one run each, after the timed steps, 64 fields to SE <= 1e-3 (Eq. 23); "
                    "wall time of the C-ABI call")
     return out

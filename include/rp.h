@@ -144,6 +144,8 @@ typedef struct rp_stats {
                                    their kernels are counted in kernel_launches */
   int kernel_path;              /* kernel path of the Chebyshev terms (rp_options.kernel
                                    values 1-4; rp_yields and rp_yields_converged) */
+  double cv_ms;                 /* rp_yields_cv: host wall time of the control-variate
+                                   work (training, mu = E[g], evaluation, estimates) */
 } rp_stats;
 
 /* Propagation plan of one field (rp_plan_field; host logic, no GPU needed). */

@@ -9,6 +9,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1078,6 +1079,12 @@ rp_status run_converged_cv(rp_system* sys, int n_fields, const double* fields, d
           tphi.push_back(pl[f][3 * i]);
         }
     std::vector<double> mu(n_fields, 0.0), vmu(n_fields, 0.0);
+    double cv_ms = 0.0;  // host wall time of the control-variate work (rp_stats.cv_ms)
+    auto now = [] { return std::chrono::steady_clock::now(); };
+    auto ms_since = [](std::chrono::steady_clock::time_point t0) {
+      return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    };
+    const auto t_train = now();
     if (tB.size() >= 2) {
       rp_cv_options net = cp.net;
       net.stream = o.stream;
@@ -1104,6 +1111,7 @@ rp_status run_converged_cv(rp_system* sys, int n_fields, const double* fields, d
     } else {
       std::fill(is_cv.begin(), is_cv.end(), 0);
     }
+    cv_ms += ms_since(t_train);
     // 3. control-variate rounds on fresh samples until the combined SE meets the target
     std::vector<double> cvout(5 * (size_t)n_fields, 0.0);
     auto cv_estimates = [&]() {
@@ -1154,13 +1162,17 @@ rp_status run_converged_cv(rp_system* sys, int n_fields, const double* fields, d
         std::vector<double> Bf(count[f], fields[f]), g(count[f]);
         std::vector<long long> sf(count[f]);
         for (long long i = 0; i < count[f]; ++i) sf[i] = first[f] + i;
+        const auto t_eval = now();
         rp_status cs = rp_cv_eval(cv, (int)count[f], Bf.data(), sf.data(), seed, o.pair_id, g.data());
+        cv_ms += ms_since(t_eval);
         if (cs != RP_OK) return cs;
         cvs[f].insert(cvs[f].end(), fresh[f].begin(), fresh[f].end());
         cvg[f].insert(cvg[f].end(), g.begin(), g.end());
         have_cv[f] += count[f];
       }
+      const auto t_est = now();
       cv_estimates();
+      cv_ms += ms_since(t_est);
       bool more = false;
       for (int f = 0; f < n_fields; ++f) {
         if (!is_cv[f] || have_cv[f] < 2) continue;
@@ -1224,6 +1236,7 @@ rp_status run_converged_cv(rp_system* sys, int n_fields, const double* fields, d
       if (M_cv) M_cv[f] = (int)have_cv[f];
     }
     fill_stats(stats, eng, total_items, R, n_c, ev.a, ev.b, o.profile != 0, d2h);
+    if (stats) stats->cv_ms = cv_ms;
   }
   ck(cudaStreamSynchronize(st), "free");
   return RP_OK;

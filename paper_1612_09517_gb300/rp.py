@@ -46,7 +46,7 @@ class rp_stats(C.Structure):
                 ("step_launches_timed", C.c_longlong), ("device_ms", C.c_double),
                 ("rows", C.c_int), ("n_cheb", C.c_int), ("h2d_bytes", C.c_longlong),
                 ("d2h_bytes", C.c_longlong), ("graph_launches", C.c_longlong),
-                ("kernel_path", C.c_int)]
+                ("kernel_path", C.c_int), ("cv_ms", C.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
