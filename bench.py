@@ -272,6 +272,11 @@ def parse():
                     help="config-2 system at 1.6 / 3.2 / 4.8 mT: variance reduction of the "
                          "learned control variate on 1000 fresh samples per field as a function "
                          "of the training-set size; one JSON line")
+    ap.add_argument("--grouped-prototype", action="store_true",
+                    help="config-3 system: time of the grouped dense-block H.psi on the tensor "
+                         "cores (the group's (8 x 2^g)^2 real block times the state, as a plain "
+                         "GEMM by the vendor library: TF32 x3 for the FP32 accuracy, BF16 for "
+                         "reference) against the matrix-free per-term kernel; one JSON line")
     ap.add_argument("--ncu-case3", action="store_true",
                     help="profiling case of the anisotropic config-3 system (Z = 2359296): "
                          "2 rows, two macro-steps, ~4 GB on the device")
@@ -425,6 +430,65 @@ def main():
                           [round(float(b), 4) for b in fb], "M": 200, **res,
                           "variance_ratio_basis_over_coherent": [round(x, 3) for x in ratio]}),
               flush=True)
+        return
+    if args.grouped_prototype:
+        # The grouped tier would apply the g innermost nuclei and both electrons
+        # as one dense complex block of dimension D = 4 x 2^g: in the layout the
+        # state is then a (Z / 2^g) x D complex matrix (the group's indices
+        # innermost), i.e. a real (Z / 2^g) x 2D matrix X, and the block a real
+        # 2D x 2D matrix; Y = X Hb^T is one plain GEMM.  Its time on the tensor
+        # cores (cuBLAS) bounds what a hand-written tcgen05 version could reach.
+        w3 = wl.config3()
+        s3 = rp.System(w3.system)
+        Z3 = s3.Z
+        st = torch.cuda.current_stream()
+        o = rp.rp_default_options(precision=rp.RP_FP32, profile=1, stream=st.cuda_stream)
+        B3 = 10.0
+        h = s3.plan(B3, w3.t_max, precision=rp.RP_FP32)["h"]
+        rp.rp_yields(s3.handle, np.array([B3]), 2, 0, h, o)  # warm-up
+        r = rp.rp_yields(s3.handle, np.array([B3]), 2, 0, 3 * h, o)
+        per_term_ms = r["stats"]["step_ms"] / max(r["stats"]["step_launches_timed"], 1)
+        row_term_us = per_term_ms * 1e3 / 2  # two rows per launch
+        n_nuc = w3.system.n_nuc
+        res = []
+        torch.backends.cuda.matmul.allow_tf32 = True
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for g in (4, 5, 6, 8):
+            D2 = 2 * 4 * (1 << g)
+            cols = Z3 // (1 << g)
+            X = torch.randn(cols, D2, device="cuda")
+            Hb = torch.randn(D2, D2, device="cuda")
+            Y = torch.empty(cols, D2, device="cuda")
+            times = {}
+            for name, dt in (("tf32", torch.float32), ("bf16", torch.bfloat16)):
+                Xc, Hc = X.to(dt), Hb.to(dt)
+                Yc = Y.to(dt)
+                for _ in range(3):
+                    torch.matmul(Xc, Hc.t(), out=Yc)
+                ev0.record(st)
+                for _ in range(10):
+                    torch.matmul(Xc, Hc.t(), out=Yc)
+                ev1.record(st)
+                torch.cuda.synchronize()
+                times[name] = ev0.elapsed_time(ev1) / 10 * 1e3  # us per GEMM
+            gemm_3x = 3 * times["tf32"]
+            share = g / n_nuc  # the group's share of the nuclei the per-term kernel applies
+            res.append({"g": g, "block_dim_real": D2, "columns": cols,
+                        "gflop_per_gemm": 2.0 * D2 * D2 * cols / 1e9,
+                        "tf32_gemm_us": times["tf32"], "tf32x3_us": gemm_3x,
+                        "bf16_gemm_us": times["bf16"],
+                        "matrix_free_share_us": share * row_term_us,
+                        "grouped_row_term_us_bound": gemm_3x + (1 - share) * row_term_us,
+                        "pays": bool(gemm_3x + (1 - share) * row_term_us < row_term_us)})
+            del X, Hb, Y
+        torch.backends.cuda.matmul.allow_tf32 = False
+        print(json.dumps({"mode": "grouped-prototype", "Z": int(Z3), "n_nuc": n_nuc,
+                          "field_mT": B3, "matrix_free_row_term_us": row_term_us,
+                          "results": res,
+                          "note": "grouped bound = 3 TF32 GEMMs (hi.hi + hi.lo + lo.hi for the "
+                                  "1e-5 FP32 bar, splits not counted) + the remaining nuclei's "
+                                  "share of the measured matrix-free term; BF16 (one GEMM) "
+                                  "misses the 1e-5 bar by orders of magnitude"}), flush=True)
         return
     if args.basis_aniso:
         w3 = wl.config3()

@@ -110,9 +110,17 @@ typedef struct rp_options {
                              4: a whole macro-step per launch on a cluster of
                              2^c CTAs per row (c <= 3) holding the row's
                              Chebyshev vectors in distributed shared memory
-                             (FP32, one isotropic system with Z / 2^c <= 3520,
+                             (FP32, one isotropic system with Z / 2^c <= 2688,
                              2^c <= 2^(number of spin-1/2 nuclei); otherwise
-                             falls back to 1) */
+                             falls back to 1);
+                             5: one persistent launch over all propagations of
+                             the call: each CTA takes (field, sample) items
+                             from a device counter and runs an item's whole
+                             horizon with its vectors in shared memory (the
+                             time integral on CUDA cores in the same CTA);
+                             Z <= 2048 FP32, 1024 FP64, deterministic 0-2,
+                             rp_yields, rp_yields_batch and the converged
+                             entries; elsewhere kernel 5 selects as 0 */
   int gram;               /* time integral (Eqs. 20, 22) of each macro-step: 0 choose
                              (2 where it applies); 1 CUDA cores (any precision);
                              2 tensor cores (FP32 single systems with the
@@ -143,7 +151,7 @@ typedef struct rp_stats {
   long long graph_launches;     /* macro-steps replayed from a CUDA graph (graph = 1);
                                    their kernels are counted in kernel_launches */
   int kernel_path;              /* kernel path of the Chebyshev terms (rp_options.kernel
-                                   values 1-4; rp_yields and rp_yields_converged) */
+                                   values 1-5; rp_yields and rp_yields_converged) */
   double cv_ms;                 /* rp_yields_cv: host wall time of the control-variate
                                    work (training, mu = E[g], evaluation, estimates) */
 } rp_stats;

@@ -174,7 +174,7 @@ int default_kernel_fp32(const HostSystem& hs, bool* cluster_ok) {
 namespace {
 
 bool bad_kernel_choice(const rp_options& o) {
-  return o.kernel < 0 || o.kernel > 4 || o.graph < 0 || o.graph > 1 || o.gram < 0 || o.gram > 2;
+  return o.kernel < 0 || o.kernel > 5 || o.graph < 0 || o.graph > 1 || o.gram < 0 || o.gram > 2;
 }
 double default_tol(int precision) { return precision == RP_FP64 ? 1e-15 : 1e-9; }
 
@@ -235,6 +235,14 @@ class YieldEngine {
     for (auto e : pev) cudaEventDestroy(e);
     drop_graphs();
     if (cap_st_) cudaStreamDestroy(cap_st_);
+    if (side_st_) {
+      cudaStreamSynchronize(side_st_);
+      cudaStreamDestroy(side_st_);
+    }
+    for (int i = 0; i < 2; ++i) {
+      if (ev_step_[i]) cudaEventDestroy(ev_step_[i]);
+      if (ev_int_[i]) cudaEventDestroy(ev_int_[i]);
+    }
   }
 
   void set_fields(const std::vector<rp::FieldPlan>& plans) {
@@ -283,6 +291,22 @@ class YieldEngine {
 
   void alloc_rows(int R) {
     R_ = R;
+    // one persistent launch over all items (kernel = 5) where every system
+    // fits one CTA's shared memory; kernel = 5 elsewhere selects as 0
+    persist_ = o_.kernel == 5 && Zslot_ <= rp::small_max_configs<T>() && o_.deterministic != 3 &&
+               !d_trace_;
+    d_err_ = ar_.get<int>(1);
+    ck(cudaMemsetAsync(d_err_, 0, sizeof(int), st_), "cudaMemsetAsync");
+    if (persist_) {
+      pctas_ = rp::persistent_ctas<T>(Zslot_, n_c_, aniso_);
+      if (pctas_ <= 0) throw CudaFail{RP_ECUDA, "persistent kernel: no device"};
+      Xp_ = ar_.get<T>((size_t)pctas_ * n_c_ * Zslot_ * 2);
+      d_counter_ = ar_.get<int>(1);
+      S_ = rp::SysTab<T>{d_ham_, d_lay_, d_kS_, nullptr, Zslot_, o_.pair_id, d_pair_, d_err_,
+                         sec_rank_, sec_scale_};
+      return;
+    }
+    const int kq = o_.kernel == 5 ? 0 : o_.kernel;
     const size_t vec = (size_t)Zslot_ * 8;
     S0_ = ar_.get<T>((size_t)R * vec);
     S1_ = ar_.get<T>((size_t)R * vec);
@@ -290,14 +314,14 @@ class YieldEngine {
     F2_ = ar_.get<T>((size_t)R * vec);
     amps_ = ar_.get<double>((size_t)R * rp::kMaxNucDev * 10 * 2);
     row_sys_ = ar_.get<int>(R);
-    small_ = (o_.kernel == 2 || (o_.kernel == 0 && Zslot_ <= rp::small_max_configs<T>())) &&
+    small_ = (kq == 2 || (kq == 0 && Zslot_ <= rp::small_max_configs<T>())) &&
              Zslot_ <= rp::small_max_configs<T>();
     // a whole macro-step per launch on a thread-block cluster per row (FP32,
     // one isotropic system whose state fits the cluster's shared memory)
     cluster_ = false;
-    if (sizeof(T) == 4 && !small_ && sys_.size() == 1 && (o_.kernel == 4 || o_.kernel == 0)) {
+    if (sizeof(T) == 4 && !small_ && sys_.size() == 1 && (kq == 4 || kq == 0)) {
       const auto& hf = *reinterpret_cast<const rp::HamDev<float>*>(&ham1_);
-      cluster_ = (o_.kernel == 4 ? rp::macro_cluster_plan(hf, nullptr)
+      cluster_ = (kq == 4 ? rp::macro_cluster_plan(hf, nullptr)
                                  : rp::macro_cluster_default(hf)) &&
                  rp::macro_cluster_max_active(hf) > 0;
     }
@@ -308,14 +332,25 @@ class YieldEngine {
     const size_t x_row = std::max<size_t>((size_t)n_c_ * Zslot_ * 2,
                                           rp::xblk_floats_per_row(Zslot_, n_c_));
     X_ = ar_.get<T>((size_t)R * x_row);
+    // cluster macro-steps leave SMs idle (clusters fill whole GPC pairs of 8):
+    // the time integral of macro-step k runs on a second stream, reading its own
+    // copy of the singlet slices, while macro-step k + 1 propagates
+    overlap_ = cluster_ && tc_gram_ && !o_.graph && !d_trace_;
+    if (overlap_) {
+      X2_ = ar_.get<T>((size_t)R * x_row);
+      ck(cudaMemsetAsync(X2_, 0, (size_t)R * x_row * sizeof(T), st_), "cudaMemsetAsync");
+      if (!side_st_) ck(cudaStreamCreateWithFlags(&side_st_, cudaStreamNonBlocking), "cudaStreamCreate");
+      for (int i = 0; i < 2; ++i) {
+        if (!ev_step_[i]) ck(cudaEventCreateWithFlags(&ev_step_[i], cudaEventDisableTiming), "cudaEventCreate");
+        if (!ev_int_[i]) ck(cudaEventCreateWithFlags(&ev_int_[i], cudaEventDisableTiming), "cudaEventCreate");
+      }
+    }
     if (tc_gram_) {
       ck(cudaMemsetAsync(X_, 0, (size_t)R * x_row * sizeof(T), st_), "cudaMemsetAsync");
       int dev = 0;
       ck(cudaGetDevice(&dev), "cudaGetDevice");
       ck(cudaDeviceGetAttribute(&n_sm_, cudaDevAttrMultiProcessorCount, dev), "cudaDeviceGetAttribute");
     }
-    d_err_ = ar_.get<int>(1);
-    ck(cudaMemsetAsync(d_err_, 0, sizeof(int), st_), "cudaMemsetAsync");
     S_ = rp::SysTab<T>{d_ham_, d_lay_, d_kS_, row_sys_, Zslot_, o_.pair_id, d_pair_, d_err_,
                        sec_rank_, sec_scale_};
     rows_.field = ar_.get<int>(R);
@@ -327,8 +362,53 @@ class YieldEngine {
     rows_.survival = rows_.integral + R;
   }
 
+  // All items in one launch of k_persistent_small: CTAs take items from a
+  // device counter, so nothing returns to the host until the last one ends.
+  void run_persistent(const std::vector<Item>& items, double* d_ps) {
+    const long long n = (long long)items.size();
+    if (n == 0) return;
+    if (n > 2000000000LL) throw CudaFail{RP_EINVAL, "too many propagations for one launch"};
+    std::vector<rp::PItem> h((size_t)n);
+    for (long long i = 0; i < n; ++i) {
+      const Item& it = items[(size_t)i];
+      h[(size_t)i] = rp::PItem{it.field, it.sys, it.n_macro, 0, it.sample, it.out};
+      row_terms += (long long)it.n_macro * n_c_;
+      // HBM: the singlet slices out and back in per macro-step
+      step_bytes_all += 2.0 * n_c_ * (double)sys_[it.sys]->Z * 2.0 * sizeof(T) * it.n_macro;
+    }
+    rp::PItem* d_items = ar_.get<rp::PItem>((size_t)n);
+    ck(cudaMemcpyAsync(d_items, h.data(), h.size() * sizeof(rp::PItem), cudaMemcpyHostToDevice, st_),
+       "h2d items");
+    h2d += (long long)(h.size() * sizeof(rp::PItem));
+    ck(cudaMemsetAsync(d_counter_, 0, sizeof(int), st_), "cudaMemsetAsync");
+    if (o_.profile) {
+      cudaEvent_t e0, e1;
+      ck(cudaEventCreate(&e0), "cudaEventCreate");
+      pev.push_back(e0);
+      ck(cudaEventCreate(&e1), "cudaEventCreate");
+      pev.push_back(e1);
+      ck(cudaEventRecord(e0, st_), "cudaEventRecord");
+    }
+    launched(rp::launch_persistent_small<T>(S_, aniso_, d_fdev_, d_coef_, d_W_, d_items, (int)n,
+                                            d_counter_, n_c_, o_.deterministic, seed_, Xp_, pctas_,
+                                            d_ps, st_),
+             "persistent kernel");
+    step_launches += 1;
+    if (o_.profile) {
+      ck(cudaEventRecord(pev.back(), st_), "cudaEventRecord");
+      pev_bytes.push_back(step_bytes_all);
+      pev_launches.push_back(1);
+    }
+    ck(cudaStreamSynchronize(st_), "kernel execution");
+  }
+
   void run(const std::vector<Item>& items, double* d_ps) {
+    if (persist_) {
+      run_persistent(items, d_ps);
+      return;
+    }
     const int R = R_;
+    if (d_trace_ || o_.graph) overlap_ = false;  // eager, single-stream macro-steps
     const long long n_items = (long long)items.size();
     std::vector<int> h_field(R, 0), h_flag(R, 0), h_sys(R, 0);
     std::vector<int2> h_win(R, make_int2(0, 0));
@@ -434,6 +514,9 @@ class YieldEngine {
         any = any || h_flag[r];
       }
       if (!any) continue;
+      // the finishing rows' integrals (and every row's metadata the side
+      // stream still reads) are complete once macro-step k is integrated
+      if (overlap_) ck(cudaStreamWaitEvent(st_, ev_int_[k & 1], 0), "cudaStreamWaitEvent");
       ck(cudaMemcpyAsync(rows_.flag, h_flag.data(), R * sizeof(int), cudaMemcpyHostToDevice, st_), "h2d flags");
       h2d += (long long)R * sizeof(int);
       launched(rp::launch_norm<T>(S_, S0_, S1_, rows_.win, rows_.flag, R, rows_.survival, st_), "norm kernel");
@@ -455,6 +538,11 @@ class YieldEngine {
       }
     }
     drop_graphs();
+    if (overlap_) {
+      // everything on the side stream before the caller's stream goes on
+      ck(cudaEventRecord(ev_int_[0], side_st_), "cudaEventRecord");
+      ck(cudaStreamWaitEvent(st_, ev_int_[0], 0), "cudaStreamWaitEvent");
+    }
     // kernels with bounded waits report a wait that gave up in the error word
     int h_err = 0;
     ck(cudaMemcpyAsync(&h_err, d_err_, sizeof(int), cudaMemcpyDeviceToHost, st_), "d2h error word");
@@ -471,9 +559,13 @@ class YieldEngine {
     sec_scale_ = scale;
   }
 
-  // Kernel path taken (rp_stats.kernel_path): 4 cluster, 2 one CTA per row,
-  // 3 staged per-term, 1 per-term.
-  int kernel_path() const { return cluster_ ? 4 : (small_ ? 2 : (o_.kernel == 3 ? 3 : 1)); }
+  // Kernel path taken (rp_stats.kernel_path): 5 persistent, 4 cluster, 2 one
+  // CTA per row, 3 staged per-term, 1 per-term.
+  int kernel_path() const {
+    return persist_ ? 5 : cluster_ ? 4 : (small_ ? 2 : (o_.kernel == 3 ? 3 : 1));
+  }
+  // Rows propagated at once: CTAs of the persistent launch, else allocated rows.
+  int rows_used() const { return persist_ ? pctas_ : R_; }
 
   // Time-resolved sums (launch_trace) after every macro-step, 4 doubles per
   // time point, with an optional electron operator; eager launches.
@@ -507,12 +599,15 @@ class YieldEngine {
          "macro-step kernel");
       n_step = 1;
     }
+    T* Xk = (overlap_ && (k & 1)) ? X2_ : X_;
     if (cluster_) {
+      // the slices of macro-step k - 2 (same buffer) must have been integrated
+      if (overlap_ && k >= 2) ck(cudaStreamWaitEvent(s, ev_int_[k & 1], 0), "cudaStreamWaitEvent");
       ck(rp::launch_macro_cluster(*reinterpret_cast<const rp::HamDev<float>*>(&ham1_),
                                   reinterpret_cast<const rp::FieldDev<float>*>(d_fdev_),
                                   rows_.field, rows_.win, k, mdev, R_,
                                   reinterpret_cast<const float*>(P), reinterpret_cast<float*>(Q),
-                                  reinterpret_cast<float*>(X_),
+                                  reinterpret_cast<float*>(Xk),
                                   reinterpret_cast<const float*>(d_coef_), n_c_, Zslot_,
                                   tc_gram_ ? 1 : 0, s),
          "cluster macro-step kernel");
@@ -528,7 +623,17 @@ class YieldEngine {
       ++n_step;
     }
     if (ev_steps) ck(cudaEventRecord(ev_steps, s), "cudaEventRecord");
-    if (tc_gram_)
+    if (overlap_) {
+      ck(cudaEventRecord(ev_step_[k & 1], s), "cudaEventRecord");
+      ck(cudaStreamWaitEvent(side_st_, ev_step_[k & 1], 0), "cudaStreamWaitEvent");
+      ck(rp::launch_gram_tc(reinterpret_cast<const float*>(Xk), d_W_, rows_.field, rows_.win, k,
+                            mdev, R_, n_c_, Zslot_,
+                            reinterpret_cast<const rp::HamDev<float>*>(d_ham_),
+                            sys_.size() == 1 ? nullptr : row_sys_, n_sm_, rows_.integral, d_err_,
+                            side_st_),
+         "tensor-core time-integral kernel");
+      ck(cudaEventRecord(ev_int_[k & 1], side_st_), "cudaEventRecord");
+    } else if (tc_gram_)
       ck(rp::launch_gram_tc(reinterpret_cast<const float*>(X_), d_W_, rows_.field, rows_.win, k,
                             mdev, R_, n_c_, Zslot_,
                             reinterpret_cast<const rp::HamDev<float>*>(d_ham_),
@@ -590,6 +695,14 @@ class YieldEngine {
   rp::HamDev<T> ham1_{};
   bool small_ = false;
   bool cluster_ = false;
+  bool overlap_ = false;
+  bool persist_ = false;
+  int pctas_ = 0;
+  T* Xp_ = nullptr;
+  int* d_counter_ = nullptr;
+  T* X2_ = nullptr;
+  cudaStream_t side_st_ = nullptr;
+  cudaEvent_t ev_step_[2] = {nullptr, nullptr}, ev_int_[2] = {nullptr, nullptr};
   const int* sec_rank_ = nullptr;
   const double* sec_scale_ = nullptr;
   rp::ElecOp trace_op_{};
@@ -671,7 +784,7 @@ void fill_stats(rp_stats* stats, const YieldEngine<T>& eng, long long items, int
   stats->graph_launches = eng.graph_launches;
   stats->row_terms = eng.row_terms;
   stats->propagations = items;
-  stats->rows = R;
+  stats->rows = eng.kernel_path() == 5 ? eng.rows_used() : R;
   stats->n_cheb = n_c;
   stats->kernel_path = eng.kernel_path();
   float ms = 0.f;
@@ -819,11 +932,11 @@ rp_status run_time_trace(rp_system* sys, double B, int M, uint64_t seed, double 
     YieldEngine<T> eng({&hs}, o, n_c, st, ar);
     eng.set_seed(seed);
     eng.set_fields(plans);
-    eng.alloc_rows(R);
-    double* d_ps = ar.get<double>(items.size() * 3);
     double* d_tr = ar.get<double>(4 * (size_t)n_times);
     ck(cudaMemsetAsync(d_tr, 0, 4 * (size_t)n_times * sizeof(double), st), "cudaMemsetAsync");
     eng.set_trace(d_tr, op);
+    eng.alloc_rows(R);
+    double* d_ps = ar.get<double>(items.size() * 3);
     eng.run(items, d_ps);
     ck(cudaMemcpyAsync(h_tr.data(), d_tr, h_tr.size() * sizeof(double), cudaMemcpyDeviceToHost, st),
        "d2h trace");
@@ -1579,7 +1692,7 @@ rp_status rp_yields(rp_system* s, int n_fields, const double* fields, int M, uin
   if (!s) return fail(RP_EINVAL, "system is NULL");
   if (n_fields < 0) return fail(RP_EINVAL, "n_fields must be >= 0");
   if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
-  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..4, gram 0..2 and graph 0 or 1");
+  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..5, gram 0..2 and graph 0 or 1");
   if (o.deterministic < 0 || o.deterministic > 3) return fail(RP_EINVAL, "deterministic must be 0, 1, 2 or 3");
   if (o.deterministic == 3 && s->hs.aniso)
     return fail(RP_EINVAL, "the J_z-sector trace (deterministic = 3) needs isotropic hyperfine couplings");
@@ -1680,7 +1793,7 @@ rp_status rp_time_trace(rp_system* s, double B, int M, uint64_t seed, double t_m
   else rp_default_options(&o);
   if (!s || !n_times) return fail(RP_EINVAL, "system or n_times is NULL");
   if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
-  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..4, gram 0..2 and graph 0 or 1");
+  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..5, gram 0..2 and graph 0 or 1");
   if (o.deterministic == 3) return fail(RP_ENOTIMPL, "rp_time_trace does not take the J_z-sector trace (deterministic = 3)");
   if (o.deterministic < 0 || o.deterministic > 2) return fail(RP_EINVAL, "deterministic must be 0, 1 or 2");
   if (o.deterministic != 1 && M < 1) return fail(RP_EINVAL, "M must be >= 1");
@@ -1723,7 +1836,7 @@ rp_status rp_time_observable(rp_system* s, double B, int M, uint64_t seed, doubl
   else rp_default_options(&o);
   if (!s || !n_times) return fail(RP_EINVAL, "system or n_times is NULL");
   if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
-  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..4, gram 0..2 and graph 0 or 1");
+  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..5, gram 0..2 and graph 0 or 1");
   if (o.deterministic == 3) return fail(RP_ENOTIMPL, "rp_time_observable does not take the J_z-sector trace (deterministic = 3)");
   if (o.deterministic < 0 || o.deterministic > 2) return fail(RP_EINVAL, "deterministic must be 0, 1 or 2");
   if (o.deterministic != 1 && M < 1) return fail(RP_EINVAL, "M must be >= 1");
@@ -1765,7 +1878,7 @@ rp_status rp_yields_converged(rp_system* s, int n_fields, const double* fields, 
   if (!s) return fail(RP_EINVAL, "system is NULL");
   if (n_fields < 0) return fail(RP_EINVAL, "n_fields must be >= 0");
   if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
-  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..4, gram 0..2 and graph 0 or 1");
+  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..5, gram 0..2 and graph 0 or 1");
   if (o.deterministic) return fail(RP_EINVAL, "rp_yields_converged samples coherent states only");
   if (!(se_target > 0.0) || !std::isfinite(se_target)) return fail(RP_EINVAL, "se_target must be positive");
   if (M_min < 2 || M_max < M_min) return fail(RP_EINVAL, "need 2 <= M_min <= M_max");
@@ -1814,7 +1927,7 @@ rp_status rp_yields_cv(rp_system* s, int n_fields, const double* fields, double 
   if (!s) return fail(RP_EINVAL, "system is NULL");
   if (n_fields < 0) return fail(RP_EINVAL, "n_fields must be >= 0");
   if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
-  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..4, gram 0..2 and graph 0 or 1");
+  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..5, gram 0..2 and graph 0 or 1");
   if (o.deterministic) return fail(RP_EINVAL, "rp_yields_cv samples coherent states only");
   if (!(se_target > 0.0) || !std::isfinite(se_target)) return fail(RP_EINVAL, "se_target must be positive");
   if (M_min < 2 || M_max < M_min) return fail(RP_EINVAL, "need 2 <= M_min <= M_max");
@@ -1854,7 +1967,7 @@ rp_status rp_yields_batch(int n_sys, rp_system* const* systems, const int* n_fie
   if (n_sys == 0) return RP_OK;
   if (!systems || !n_fields || !fields || !M || !t_max || !out) return fail(RP_EINVAL, "NULL argument");
   if (o.precision != RP_FP64 && o.precision != RP_FP32) return fail(RP_EINVAL, "bad precision");
-  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..4, gram 0..2 and graph 0 or 1");
+  if (bad_kernel_choice(o)) return fail(RP_EINVAL, "kernel must be 0..5, gram 0..2 and graph 0 or 1");
   if (o.deterministic) return fail(RP_EINVAL, "rp_yields_batch samples coherent states only");
   if (o.sample_offset < 0) return fail(RP_EINVAL, "sample_offset must be >= 0");
   long long total = 0;

@@ -2,6 +2,7 @@
 // coherent-state sampling (Eqs. 15, 17-19), matrix-free H.psi fused with the
 // Chebyshev recurrence (Eqs. 1-4, 13), the singlet Gram / exact time integral
 // (Eqs. 20, 22) and the per-field averages with standard errors (Eqs. 18, 23).
+#include <algorithm>
 #include <cstring>
 
 #include "rp_kernels.cuh"
@@ -1602,6 +1603,35 @@ __device__ __forceinline__ double u53(uint32_t hi, uint32_t lo) {
   return ((double)(hi >> 5) * 67108864.0 + (double)(lo >> 6)) * (1.0 / 9007199254740992.0);
 }
 
+// Components c_j (o[2 j], o[2 j + 1], j = 0 .. 2I) of the coherent state of the
+// nucleus at layout position p for sample s: Philox draw of the direction
+// (counter (input index, s_lo, s_hi, pair), key seed; cos theta = 1 - 2 u1,
+// phi = 2 pi u2, Eq. 17) and c_j = sqrt(C(2I, j)) cos^{2I-j}(theta/2)
+// sin^j(theta/2) e^{i j phi} (Eq. 15); u receives (u1, u2).
+__device__ __forceinline__ void coherent_amp(const LayoutDev& L, int p, uint32_t pair,
+                                             unsigned long long s, uint64_t seed, double* o,
+                                             double* u) {
+  const int k = L.input_index[p];
+  uint32_t c[4] = {(uint32_t)k, (uint32_t)(s & 0xFFFFFFFFull), (uint32_t)(s >> 32), pair};
+  philox4x32_10(c, (uint32_t)(seed & 0xFFFFFFFFull), (uint32_t)(seed >> 32));
+  const double u1 = u53(c[0], c[1]), u2 = u53(c[2], c[3]);
+  u[0] = u1;
+  u[1] = u2;
+  const double ch = sqrt(1.0 - u1), sh = sqrt(u1);  // cos(theta/2), sin(theta/2)
+  const int d = L.d[p], twoI = d - 1;
+  double binom = 1.0;  // C(2I, j)
+  for (int j = 0; j < d; ++j) {
+    if (j > 0) binom = binom * (double)(twoI - j + 1) / (double)j;
+    double mag = sqrt(binom);
+    for (int i = 0; i < twoI - j; ++i) mag *= ch;
+    for (int i = 0; i < j; ++i) mag *= sh;
+    double sn, cs;
+    sincospi(2.0 * (double)j * u2, &sn, &cs);
+    o[2 * j] = mag * cs;
+    o[2 * j + 1] = mag * sn;
+  }
+}
+
 // One thread per (row, nucleus position): Philox draw of the direction
 // (cos theta = 1 - 2 u1, phi = 2 pi u2; uniform on the sphere, Eq. 17) and the
 // coherent-state components c_j = sqrt(C(2I, j)) cos^{2I-j}(theta/2)
@@ -1618,28 +1648,13 @@ __global__ void k_coherent_amps(const SysTab<T> S, const long long* __restrict__
   const LayoutDev& L = S.lay[sidx];
   if (p >= L.n_nuc) return;
   const uint32_t pair = S.pair_of ? S.pair_of[sidx] : S.pair_base + (uint32_t)sidx;
-  const int k = L.input_index[p];
-  const unsigned long long s = (unsigned long long)row_sample[r];
-  uint32_t c[4] = {(uint32_t)k, (uint32_t)(s & 0xFFFFFFFFull), (uint32_t)(s >> 32), pair};
-  philox4x32_10(c, (uint32_t)(seed & 0xFFFFFFFFull), (uint32_t)(seed >> 32));
-  const double u1 = u53(c[0], c[1]), u2 = u53(c[2], c[3]);
-  if (uv) {
-    uv[((size_t)r * L.n_nuc + k) * 2] = u1;
-    uv[((size_t)r * L.n_nuc + k) * 2 + 1] = u2;
-  }
-  const double ch = sqrt(1.0 - u1), sh = sqrt(u1);  // cos(theta/2), sin(theta/2)
-  const int d = L.d[p], twoI = d - 1;
   double* o = amps + ((size_t)r * kMaxNucDev + p) * 10 * 2;
-  double binom = 1.0;  // C(2I, j)
-  for (int j = 0; j < d; ++j) {
-    if (j > 0) binom = binom * (double)(twoI - j + 1) / (double)j;
-    double mag = sqrt(binom);
-    for (int i = 0; i < twoI - j; ++i) mag *= ch;
-    for (int i = 0; i < j; ++i) mag *= sh;
-    double sn, cs;
-    sincospi(2.0 * (double)j * u2, &sn, &cs);
-    o[2 * j] = mag * cs;
-    o[2 * j + 1] = mag * sn;
+  double u[2];
+  coherent_amp(L, p, pair, (unsigned long long)row_sample[r], seed, o, u);
+  if (uv) {
+    const int k = L.input_index[p];
+    uv[((size_t)r * L.n_nuc + k) * 2] = u[0];
+    uv[((size_t)r * L.n_nuc + k) * 2 + 1] = u[1];
   }
 }
 
@@ -1692,6 +1707,263 @@ __global__ void __launch_bounds__(256) k_init_state(const SysTab<T> S,
   v[2] = {(T)(-s * pr), (T)(-s * pi)};
   v[3] = {T(0), T(0)};
   store4(psi + (size_t)r * S.Zslot * 8 + (size_t)m * 8, v);
+}
+
+// ---- one persistent launch over all work items of small systems ----
+// Each CTA takes (system, field, sample) items from a device counter until
+// none is left (device-side refill) and runs each item's whole propagation on
+// chip: coherent-state amplitudes (Eqs. 15, 17, 19) and psi(0) in shared
+// memory; per macro-step the n_c Chebyshev terms with the row in shared
+// memory (as k_macro_small), the singlet slices in the CTA's own global
+// scratch, and the exact time integral of the step (Eqs. 20, 22: partial
+// Gram over 4 x 4 tiles (n, m), contracted with W in FP64); psi(h) becomes
+// the next step's phi_0 by swapping buffers; at the end survival |psi(T)|^2,
+// phi_S = k_S integral, phi_T = 1 - survival - phi_S into the per-sample
+// output.  Items are independent, so no CTA waits for another.
+constexpr int kPersistThreads = 256;
+constexpr int kPersistGramZc = 32;  // configurations per staged Gram chunk
+
+template <typename T>
+size_t persist_smem_bytes(long long Zs, int n_c) {
+  const int zc = sizeof(T) == 4 ? kPersistGramZc : kPersistGramZc / 2;
+  return (size_t)3 * 4 * Zs * sizeof(Cx<T>) + (size_t)zc * (n_c + 2) * sizeof(Cx<T>);
+}
+
+template <typename T, bool ANISO>
+__global__ void __launch_bounds__(kPersistThreads) k_persistent_small(
+    const SysTab<T> S, const FieldDev<T>* __restrict__ fields, const T* __restrict__ coef,
+    const double* __restrict__ W, const PItem* __restrict__ items, int n_items,
+    int* __restrict__ counter, int n_c, int deterministic, uint64_t seed,
+    T* __restrict__ Xscratch, double* __restrict__ per_sample) {
+  extern __shared__ __align__(16) unsigned char psmem[];
+  __shared__ HamDev<T> Hs;
+  __shared__ double amps[kMaxNucDev * 10 * 2];
+  __shared__ double red[kPersistThreads];
+  __shared__ int s_item;
+  const int Zs = (int)S.Zslot;
+  const int zc = sizeof(T) == 4 ? kPersistGramZc : kPersistGramZc / 2;
+  const int ldn = n_c + 2;
+  Cx<T>* buf0 = reinterpret_cast<Cx<T>*>(psmem);
+  Cx<T>* buf1 = buf0 + (size_t)4 * Zs;
+  Cx<T>* buf2 = buf1 + (size_t)4 * Zs;
+  Cx<T>* sx = buf2 + (size_t)4 * Zs;  // Gram staging [zc][ldn]
+  T* xr = Xscratch + (size_t)blockIdx.x * n_c * Zs * 2;
+  const int tid = threadIdx.x;
+  // the 4 x 4 tile (ti, tj), ti <= tj, of the Gram this thread sums
+  const int nt = n_c / 4, tiles = nt * (nt + 1) / 2;
+  int ti = 0, tj = 0;
+  {
+    int q = tid % (tiles > 0 ? tiles : 1);
+    for (int i = 0; i < nt; ++i) {
+      const int cnt = nt - i;
+      if (q < cnt) {
+        ti = i;
+        tj = i + q;
+        break;
+      }
+      q -= cnt;
+    }
+  }
+  const int groups = tiles >= kPersistThreads ? 1 : kPersistThreads / tiles;
+  const int g = tid / (tiles > 0 ? tiles : 1);
+  const bool tile_on = tid < tiles * groups;
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    if (it >= n_items) break;  // the same for the whole CTA
+    const PItem I = items[it];
+    {
+      const int4* src = reinterpret_cast<const int4*>(S.ham + I.sys);
+      int4* dst = reinterpret_cast<int4*>(&Hs);
+      for (int i = tid; i < (int)(sizeof(HamDev<T>) / 16); i += blockDim.x) dst[i] = src[i];
+    }
+    const LayoutDev& L = S.lay[I.sys];
+    if (!deterministic && tid < L.n_nuc) {
+      double u[2];
+      const uint32_t pair = S.pair_of ? S.pair_of[I.sys] : S.pair_base + (uint32_t)I.sys;
+      coherent_amp(L, tid, pair, (unsigned long long)I.sample, seed, amps + tid * 20, u);
+    }
+    __syncthreads();
+    const int Z = (int)Hs.Z;
+    // psi(0) = |S> x prod_p c_p(j_p) (Eq. 19) or |S, m0> (Eq. 13) in buffer 0
+    Cx<T>* P = buf0;   // phi_0 = psi(t)
+    Cx<T>* B = buf1;   // phi_n of odd parity
+    Cx<T>* A = buf2;   // accumulator psi(t + h)
+    for (int m = tid; m < Z; m += blockDim.x) {
+      double pr = 1.0, pi = 0.0;
+      if (deterministic) {
+        pr = (m == I.sample) ? 1.0 : 0.0;
+      } else {
+        int q = m;
+        for (int p = 0; p < L.n_nuc; ++p) {
+          const int d = L.d[p];
+          const int j = q % d;
+          q /= d;
+          const double ar = amps[(p * 10 + j) * 2], ai = amps[(p * 10 + j) * 2 + 1];
+          const double nr = pr * ar - pi * ai;
+          pi = pr * ai + pi * ar;
+          pr = nr;
+        }
+      }
+      const double s = 0.70710678118654752440;
+      Cx<T> v[4];
+      v[0] = {T(0), T(0)};
+      v[1] = {(T)(s * pr), (T)(s * pi)};
+      v[2] = {(T)(-s * pr), (T)(-s * pi)};
+      v[3] = {T(0), T(0)};
+      tile_put(P, Z, m, v);
+    }
+    __syncthreads();
+    const FieldDev<T> F = fields[I.field];
+    const T* cf = coef + (size_t)I.field * n_c * 4;
+    const T* cl = cf + 2 * n_c;
+    const double* Wf = W + (size_t)I.field * n_c * n_c * 2;
+    double integral = 0.0;  // thread 0
+    for (int km = 0; km < I.n_macro; ++km) {
+      // ---- one macro-step: psi(t) in P, psi(t + h) into A, phi_n in P / B ----
+      {
+        const T c0r = cf[0], c0i = cf[1];
+        for (int m = tid; m < Z; m += blockDim.x) {
+          Cx<T> a[4];
+          tile_get(P, Z, m, a);
+          Cx<T> s4[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            s4[e] = {T(0), T(0)};
+            if (sizeof(T) == 4) cmac(s4[e], cl[0], cl[1], a[e]);
+            cmac(s4[e], c0r, c0i, a[e]);
+          }
+          tile_put(A, Z, m, s4);
+          store_singlet(xr + (size_t)m * 2, a);
+        }
+        __syncthreads();
+        for (int n = 1; n < n_c; ++n) {
+          const Cx<T>* cur = (n & 1) ? P : B;  // phi_{n-1}
+          Cx<T>* nxt = (n & 1) ? B : P;        // phi_{n-2}, then phi_n
+          const T cr = cf[2 * n], ci = cf[2 * n + 1];
+          for (int m = tid; m < Z; m += blockDim.x) {
+            Cx<T> a[4], z[4], ph[4];
+            tile_get(cur, Z, m, a);
+            apply_local<T, ANISO>(Hs, F, (unsigned)m, a, cur, Z, z);
+            if (n == 1) {
+#pragma unroll
+              for (int e = 0; e < 4; ++e) ph[e] = z[e];
+            } else {
+              Cx<T> pv[4];
+              tile_get(nxt, Z, m, pv);
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                ph[e].re = T(2) * z[e].re - pv[e].re;
+                ph[e].im = T(2) * z[e].im - pv[e].im;
+              }
+            }
+            Cx<T> s4[4];
+            tile_get(A, Z, m, s4);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              if (sizeof(T) == 4) cmac(s4[e], cl[2 * n], cl[2 * n + 1], ph[e]);
+              cmac(s4[e], cr, ci, ph[e]);
+            }
+            tile_put(A, Z, m, s4);
+            store_singlet(xr + ((size_t)n * Zs + m) * 2, ph);
+            if (n < n_c - 1) tile_put(nxt, Z, m, ph);
+          }
+          __syncthreads();
+        }
+      }
+      // ---- exact time integral of the step: Re sum_nm W_nm G_nm ----
+      {
+        // sums in T within a chunk (pr_, pi_) and in a second T accumulator
+        // across chunks (ar_, ai_), as in k_gram_integrate
+        T ar_[4][4], ai_[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) ar_[i][j] = ai_[i][j] = T(0);
+        for (int c0 = 0; c0 < Z; c0 += zc) {
+          for (int idx = tid; idx < n_c * zc; idx += blockDim.x) {
+            const int nn = idx / zc, zz = idx - nn * zc;
+            const int z = c0 + zz;
+            Cx<T> v = {T(0), T(0)};
+            if (z < Z) {
+              v.re = xr[((size_t)nn * Zs + z) * 2];
+              v.im = xr[((size_t)nn * Zs + z) * 2 + 1];
+            }
+            sx[zz * ldn + nn] = v;
+          }
+          __syncthreads();
+          if (tile_on) {
+            T pr_[4][4], pi_[4][4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int j = 0; j < 4; ++j) pr_[i][j] = pi_[i][j] = T(0);
+            for (int zz = g; zz < zc; zz += groups) {
+              const Cx<T>* row = sx + zz * ldn;
+              Cx<T> xi[4], xj[4];
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                xi[i] = row[4 * ti + i];
+                xj[i] = row[4 * tj + i];
+              }
+#pragma unroll
+              for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                  pr_[i][j] = fma(xi[i].re, xj[j].re, fma(xi[i].im, xj[j].im, pr_[i][j]));
+                  pi_[i][j] = fma(xi[i].re, xj[j].im, fma(-xi[i].im, xj[j].re, pi_[i][j]));
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int j = 0; j < 4; ++j) {
+                ar_[i][j] += pr_[i][j];
+                ai_[i][j] += pi_[i][j];
+              }
+          }
+          __syncthreads();
+        }
+        double sum = 0.0;
+        if (tile_on) {
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int nn = 4 * ti + i, mm = 4 * tj + j;
+              if (nn > mm) continue;
+              const size_t w = ((size_t)nn * n_c + mm) * 2;
+              const double v = Wf[w] * (double)ar_[i][j] - Wf[w + 1] * (double)ai_[i][j];
+              sum += (nn == mm) ? v : 2.0 * v;
+            }
+        }
+        const double tot = block_sum<kPersistThreads>(sum, red);
+        if (tid == 0) integral += tot;
+        __syncthreads();
+      }
+      // psi(t + h) is phi_0 of the next step
+      Cx<T>* t_ = P;
+      P = A;
+      A = t_;
+    }
+    double nn = 0.0;
+    for (int m = tid; m < Z; m += blockDim.x) {
+      Cx<T> a[4];
+      tile_get(P, Z, m, a);
+#pragma unroll
+      for (int e = 0; e < 4; ++e)
+        nn += (double)a[e].re * (double)a[e].re + (double)a[e].im * (double)a[e].im;
+    }
+    const double surv = block_sum<kPersistThreads>(nn, red);
+    if (tid == 0) {
+      const double phS = S.k_S[I.sys] * integral;
+      per_sample[I.out * 3] = phS;
+      per_sample[I.out * 3 + 1] = 1.0 - surv - phS;
+      per_sample[I.out * 3 + 2] = surv;
+    }
+    __syncthreads();
+  }
 }
 
 // Advances the device-side macro-step counter read by graph-replayed kernels.
@@ -1989,6 +2261,45 @@ int macro_cluster_max_active(const HamDev<float>& H) {
 }
 
 template <typename T>
+size_t persistent_smem(long long Zs, int n_c) {
+  return persist_smem_bytes<T>(Zs, n_c);
+}
+
+template <typename T>
+int persistent_ctas(long long Zs, int n_c, int aniso) {
+  const size_t smem = persist_smem_bytes<T>(Zs, n_c);
+  int dev = 0, n_sm = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  static std::atomic<unsigned long long> attr_done[2];
+  auto kf = aniso ? k_persistent_small<T, true> : k_persistent_small<T, false>;
+  if (smem_attr_once((const void*)kf, (int)persist_smem_bytes<T>(SmallCfg<T>::kMax, 88),
+                     attr_done[aniso ? 1 : 0]) != cudaSuccess)
+    return 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, kPersistThreads, smem) !=
+      cudaSuccess)
+    return 0;
+  return n_sm * std::max(per_sm, 1);
+}
+
+template <typename T>
+cudaError_t launch_persistent_small(const SysTab<T>& S, int aniso, const FieldDev<T>* fields,
+                                    const T* coef, const double* W, const PItem* items,
+                                    int n_items, int* counter, int n_c, int deterministic,
+                                    uint64_t seed, T* Xscratch, int ctas, double* per_sample,
+                                    cudaStream_t st) {
+  if (n_items == 0 || ctas == 0) return cudaSuccess;
+  if (S.Zslot > SmallCfg<T>::kMax) return cudaErrorInvalidValue;
+  if (n_c % 4 != 0 || n_c > 88) return cudaErrorInvalidValue;  // <= 253 Gram tiles
+  const size_t smem = persist_smem_bytes<T>(S.Zslot, n_c);
+  auto kf = aniso ? k_persistent_small<T, true> : k_persistent_small<T, false>;
+  // the shared-memory attribute was set by persistent_ctas, which gave `ctas`
+  kf<<<ctas, kPersistThreads, smem, st>>>(S, fields, coef, W, items, n_items, counter, n_c,
+                                          deterministic, seed, Xscratch, per_sample);
+  return cudaGetLastError();
+}
+
+template <typename T>
 cudaError_t launch_gram_integrate(const SysTab<T>& S, const T* X, const double* W,
                                   const int* row_field, const int2* row_win, int macro,
                                   const int* macro_dev, int rows, int n_c, double* integral,
@@ -2084,6 +2395,12 @@ template cudaError_t launch_gram_integrate<float>(const SysTab<float>&, const fl
                                                   const int*, const int2*, int, const int*, int,
                                                   int, double*, cudaStream_t);
 template int small_max_configs<float>();
+template size_t persistent_smem<float>(long long, int);
+template int persistent_ctas<float>(long long, int, int);
+template cudaError_t launch_persistent_small<float>(const SysTab<float>&, int, const FieldDev<float>*,
+                                                    const float*, const double*, const PItem*, int,
+                                                    int*, int, int, uint64_t, float*, int, double*,
+                                                    cudaStream_t);
 template cudaError_t launch_macro_small<float>(const SysTab<float>&, const HamDev<float>*, int,
                                                const FieldDev<float>*, const int*, const int2*, int,
                                                const int*, int, const float*, float*, float*,
@@ -2107,6 +2424,12 @@ template cudaError_t launch_gram_integrate<double>(const SysTab<double>&, const 
                                                   const int*, const int2*, int, const int*, int,
                                                   int, double*, cudaStream_t);
 template int small_max_configs<double>();
+template size_t persistent_smem<double>(long long, int);
+template int persistent_ctas<double>(long long, int, int);
+template cudaError_t launch_persistent_small<double>(const SysTab<double>&, int, const FieldDev<double>*,
+                                                     const double*, const double*, const PItem*, int,
+                                                     int*, int, int, uint64_t, double*, int, double*,
+                                                     cudaStream_t);
 template cudaError_t launch_macro_small<double>(const SysTab<double>&, const HamDev<double>*, int,
                                                const FieldDev<double>*, const int*, const int2*, int,
                                                const int*, int, const double*, double*, double*,

@@ -138,6 +138,31 @@ cudaError_t launch_macro_small(const SysTab<T>& S, const HamDev<T>* one, int ani
                                const int2* row_win, int macro, const int* macro_dev, int rows,
                                const T* P, T* Q, T* X, const T* coef, int n_c, cudaStream_t st);
 
+// A work item of the persistent launch: field index, system index, macro-steps,
+// Philox sample (or basis index) and the slot in the per-sample output.
+struct PItem {
+  int field, sys, n_macro, pad;
+  long long sample, out;
+};
+
+// One launch over all n_items work items of small systems (S.Zslot <=
+// small_max_configs<T>()): each CTA takes items from *counter (zero before the
+// launch) and propagates each item's whole horizon on chip, writing phi_S,
+// phi_T and survival to per_sample[3 out ..] (see k_persistent_small).
+// Xscratch holds n_c x Zslot complex per CTA; persistent_ctas gives the grid
+// (CTAs resident at once; it also sets the kernel's shared-memory attribute,
+// so it runs before the launch), persistent_smem the shared memory of a CTA.
+template <typename T>
+size_t persistent_smem(long long Zs, int n_c);
+template <typename T>
+int persistent_ctas(long long Zs, int n_c, int aniso);
+template <typename T>
+cudaError_t launch_persistent_small(const SysTab<T>& S, int aniso, const FieldDev<T>* fields,
+                                    const T* coef, const double* W, const PItem* items,
+                                    int n_items, int* counter, int n_c, int deterministic,
+                                    uint64_t seed, T* Xscratch, int ctas, double* per_sample,
+                                    cudaStream_t st);
+
 // A whole macro-step of every active row of one isotropic FP32 system on a
 // thread-block cluster per row, the row's Chebyshev vectors in distributed
 // shared memory (see k_macro_cluster): reads psi from P, writes the propagated

@@ -8,7 +8,8 @@
 //           macro-step per launch with the row in shared memory (only where
 //           Z fits), 4 = a whole macro-step per launch with the row in the
 //           distributed shared memory of a thread-block cluster (FP32
-//           isotropic systems that fit);
+//           isotropic systems that fit), 5 = one persistent launch over all
+//           propagations (only where Z fits one CTA; graph has no effect);
 //   n_cheb  terms per macro-step (the planner then picks the step h that
 //           meets the tolerance: more terms, longer steps, a larger
 //           n_cheb x n_cheb time-integral Gram and more singlet slices);
@@ -158,6 +159,7 @@ rp_status rp_tune(rp_system* s, double B, int rows, const rp_options* base, rp_o
     for (int g = 0; g <= 1; ++g) {
       cands.push_back({1, nc, g});
       if (Z <= small_max) cands.push_back({2, nc, g});
+      if (Z <= small_max && g == 0) cands.push_back({5, nc, 0});
       if (staged) cands.push_back({3, nc, g});
       if (cluster_ok && Z > small_max) cands.push_back({4, nc, g});
     }

@@ -176,7 +176,7 @@ def test_option_validation_without_gpu():
     work: kernel path, time-integral path, graph replay, sampling mode; the
     autotuner needs two rows; basis-index draws need a positive Z."""
     sy = rp.System(wl.config1().system)
-    for kw, msg in ((dict(kernel=5), "kernel"), (dict(kernel=-1), "kernel"), (dict(gram=3), "gram"),
+    for kw, msg in ((dict(kernel=6), "kernel"), (dict(kernel=-1), "kernel"), (dict(gram=3), "gram"),
                     (dict(graph=2), "graph"), (dict(deterministic=4), "deterministic")):
         with pytest.raises(rp.RPError, match=msg):
             sy.yields([0.0], 4, 0, 1.0, **kw)

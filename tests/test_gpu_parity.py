@@ -110,14 +110,18 @@ def test_apply_h_matches_dense(name, mk, prec):
 
 # ----------------------------------------------------------- yields, config 1
 
+@pytest.mark.parametrize("kernel", [0, 5])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_config1_per_sample_parity(prec):
-    """Config 1 in full (11 fields in 0-5 mT, M = 64, seed 0, T = 10 us)."""
+def test_config1_per_sample_parity(prec, kernel):
+    """Config 1 in full (11 fields in 0-5 mT, M = 64, seed 0, T = 10 us), in
+    the default launch form and in one persistent launch (kernel 5)."""
     rp = _rp()
     w = wl.config1()
     s = w.system
     sy = rp.System(s)
-    res = sy.yields(w.fields, w.M, w.seed, w.t_max, per_sample=True, precision=prec)
+    res = sy.yields(w.fields, w.M, w.seed, w.t_max, per_sample=True, precision=prec, kernel=kernel)
+    if kernel == 5:
+        assert res["stats"]["kernel_path"] == 5 and res["stats"]["step_launches"] == 1
     psi0 = coherent.sample_states(s, w.seed, range(w.M))
     worst = 0.0
     for i, B in enumerate(w.fields):
@@ -207,12 +211,13 @@ def test_sector_trace_matches_oracle_and_basis_states(name, mk, prec):
         assert np.allclose(r3["per_sample"][:, i, :], want, rtol=tol, atol=tol * 1e-2), i
 
 
-@pytest.mark.parametrize("kernel", [1, 2])
+@pytest.mark.parametrize("kernel", [1, 2, 5])
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 @pytest.mark.parametrize("name,mk", MIXED[1:], ids=[m[0] for m in MIXED[1:]])
 def test_mixed_systems_per_sample(name, mk, prec, kernel):
     """Anisotropic tensors, spin 1 and 3/2, J != 0, k_S != k_T, no nuclei, ragged Z;
-    per-term launches (kernel 1) and whole macro-steps on chip (kernel 2)."""
+    per-term launches (kernel 1), whole macro-steps on chip (kernel 2) and
+    whole propagations in one persistent launch (kernel 5)."""
     rp = _rp()
     s = mk()
     sy = rp.System(s)
@@ -347,9 +352,57 @@ def test_kernel_paths_agree(prec):
         sy = rp.System(s)
         a = sy.yields([0.0, 2.0], 4, 3, 1.0, per_sample=True, precision=prec, kernel=1)
         b = sy.yields([0.0, 2.0], 4, 3, 1.0, per_sample=True, precision=prec, kernel=2)
+        c = sy.yields([0.0, 2.0], 4, 3, 1.0, per_sample=True, precision=prec, kernel=5)
         tol = 1e-12 if prec == "fp64" else 2e-6
         assert np.allclose(a["per_sample"], b["per_sample"], rtol=tol, atol=tol * 1e-2)
+        assert np.allclose(a["per_sample"], c["per_sample"], rtol=tol, atol=tol * 1e-2)
         assert b["stats"]["step_launches"] < a["stats"]["step_launches"]
+        assert c["stats"]["kernel_path"] == 5 and c["stats"]["step_launches"] == 1
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_persistent_launch_edges(prec):
+    """One persistent launch (kernel 5): the largest Z it takes (2048 FP32,
+    1024 FP64), more items than CTAs with uneven horizons (fields of different
+    step counts share the launch), the basis-state trace (deterministic 1),
+    an uneven batch, and a system too large for it (selects as kernel 0)."""
+    rp = _rp()
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    n_half = 11 if prec == "fp32" else 10
+    top = wl.random_isotropic(6, n_half - 6, two_I=[1] * n_half, seed=45, k_S=0.8, k_T=2.0, J=0.2)
+    sy = rp.System(top)
+    a = sy.yields([0.0, 6.0], 3, 9, 0.6, per_sample=True, precision=prec, kernel=1)
+    c = sy.yields([0.0, 6.0], 3, 9, 0.6, per_sample=True, precision=prec, kernel=5)
+    assert c["stats"]["kernel_path"] == 5
+    assert np.allclose(a["per_sample"], c["per_sample"], rtol=tol, atol=tol * 1e-2)
+    # many items per CTA, fields with different macro-step counts
+    s = wl.random_isotropic(2, 2, two_I=[1, 2, 1, 1], k_S=1.0, k_T=3.0, J=0.2, seed=7)
+    sy = rp.System(s)
+    fields = [0.0, 1.0, 4.0, 20.0]
+    a = sy.yields(fields, 400, 5, 2.0, per_sample=True, precision=prec, kernel=2)
+    c = sy.yields(fields, 400, 5, 2.0, per_sample=True, precision=prec, kernel=5)
+    assert c["stats"]["propagations"] > c["stats"]["rows"]
+    assert np.allclose(a["per_sample"], c["per_sample"], rtol=tol, atol=tol * 1e-2)
+    # basis-state trace (Eq. 14) against the oracle's trace
+    a = sy.yields(fields[:2], 0, 0, 2.0, per_sample=True, precision=prec, deterministic=1, kernel=5)
+    for i, B in enumerate(fields[:2]):
+        ref = dense.trace_yields(s, B, 2.0)
+        assert abs(a["out"][i, 0] - ref[0]) < TOL[prec]
+    # uneven batch in one launch per group
+    systems = [wl.config1().system, wl.random_anisotropic(2, 1, two_I=[1, 2, 1], k_S=2.0, k_T=0.5,
+                                                          J=0.3, seed=40)]
+    sys_h = [rp.System(x) for x in systems]
+    fl = [np.array([0.0, 2.0]), np.array([1.0])]
+    o5 = rp.rp_default_options(precision=prec, pair_id=10, kernel=5)
+    o2 = rp.rp_default_options(precision=prec, pair_id=10, kernel=2)
+    r5 = rp.rp_yields_batch(sys_h, fl, [5, 3], [2.0, 1.5], 77, o5)
+    r2 = rp.rp_yields_batch(sys_h, fl, [5, 3], [2.0, 1.5], 77, o2)
+    for x in range(2):
+        assert np.allclose(r5["out"][x], r2["out"][x], rtol=tol, atol=tol * 1e-2)
+    # too large for one CTA: kernel 5 selects as kernel 0
+    big = wl.random_isotropic(5, 5, two_I=[1, 1, 2, 1, 1, 2, 1, 2, 1, 1], k_S=1.5, k_T=0.6, seed=49)
+    r = rp.System(big).yields([1.0], 2, 3, 0.2, precision=prec, kernel=5)
+    assert r["stats"]["kernel_path"] != 5
 
 
 # systems the cluster macro-step kernel splits over 1, 2, 4 and 8 CTAs
