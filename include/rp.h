@@ -95,7 +95,9 @@ typedef struct rp_options {
   uint32_t pair_id;       /* Philox counter word 3 (radical-pair id) */
   int profile;            /* 1: time the H.psi step kernels with CUDA events */
   void* stream;           /* cudaStream_t, NULL: the legacy default stream */
-  int kernel;             /* 0: choose (2 where Z fits one CTA's shared memory; 4
+  int kernel;             /* 0: choose (5 where 128 <= Z <= 1024, or a batch of
+                             several systems fits one CTA, and graph = 0; 2
+                             where Z fits one CTA's shared memory otherwise; 4
                              for the FP32 shapes with a compiled cluster
                              instance -- 8 spin-1/2 and 4 spin-1 nuclei,
                              isotropic, one system; else 1);

@@ -166,8 +166,15 @@ int default_kernel_fp32(const HostSystem& hs, bool* cluster_ok) {
   const HamDev<float> hf = make_ham<float>(hs);
   const bool ok = macro_cluster_plan(hf, nullptr);
   if (cluster_ok) *cluster_ok = ok;
-  if (hs.Z <= small_max_configs<float>()) return 2;
+  if (hs.Z <= small_max_configs<float>()) return persistent_default(hs.Z, 1) ? 5 : 2;
   return macro_cluster_default(hf) ? 4 : 1;
+}
+
+// kernel = 0 runs the persistent launch (kernel 5) for systems that fit one
+// CTA with 128 <= Z <= 1024, and for batches of several such systems up to
+// the size limit (measured faster than the on-chip macro-step launches).
+bool persistent_default(long long Zslot, int n_systems) {
+  return Zslot >= 128 && (Zslot <= 1024 || n_systems > 1);
 }
 }  // namespace rp
 
@@ -292,9 +299,13 @@ class YieldEngine {
   void alloc_rows(int R) {
     R_ = R;
     // one persistent launch over all items (kernel = 5) where every system
-    // fits one CTA's shared memory; kernel = 5 elsewhere selects as 0
-    persist_ = o_.kernel == 5 && Zslot_ <= rp::small_max_configs<T>() && o_.deterministic != 3 &&
-               !d_trace_;
+    // fits one CTA's shared memory; kernel = 5 elsewhere selects as 0.
+    // kernel = 0 (without graph replay, which asks for macro-step launches)
+    // takes it where it measured faster than one launch per macro-step:
+    // 128 <= Z <= 1024, and batches of several systems
+    const bool fits = Zslot_ <= rp::small_max_configs<T>() && o_.deterministic != 3 && !d_trace_;
+    persist_ = fits && (o_.kernel == 5 || (o_.kernel == 0 && !o_.graph &&
+                                           rp::persistent_default(Zslot_, (int)sys_.size())));
     d_err_ = ar_.get<int>(1);
     ck(cudaMemsetAsync(d_err_, 0, sizeof(int), st_), "cudaMemsetAsync");
     if (persist_) {

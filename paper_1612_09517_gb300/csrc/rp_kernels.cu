@@ -26,6 +26,29 @@ __device__ __forceinline__ void rmac(Cx<T>& y, T g, const Cx<T>& q) {
   y.im = fma(g, q.im, y.im);
 }
 
+// FP32: (re, im) as one packed pair (fma.rn.f32x2 of sm_100+, two fused
+// multiply-adds per instruction).  Each lane rounds as fma() does, so results
+// are bit-identical to the scalar form above.  (cmac stays scalar: its packed
+// form needs the swapped pair (im, re) and measured slower.)
+// The packed form of cmac for FP32 (same two rounding steps, bit-identical):
+// y += (ar, -ai).(re, im) on the pair (q.im, q.re), then (ar, ar).(q.re, q.im).
+// The pair (im, re) costs two moves; it pays where the coefficients are
+// loop-invariant (the cluster kernel) and not elsewhere (measured).
+__device__ __forceinline__ void cmac_packed(Cx<float>& y, float ar, float ai, const Cx<float>& q) {
+  const float2 t = __ffma2_rn(make_float2(-ai, ai), make_float2(q.im, q.re),
+                              make_float2(y.re, y.im));
+  const float2 s = __ffma2_rn(make_float2(ar, ar), make_float2(q.re, q.im), t);
+  y.re = s.x;
+  y.im = s.y;
+}
+
+template <>
+__device__ __forceinline__ void rmac<float>(Cx<float>& y, float g, const Cx<float>& q) {
+  const float2 s = __ffma2_rn(make_float2(g, g), make_float2(q.re, q.im), make_float2(y.re, y.im));
+  y.re = s.x;
+  y.im = s.y;
+}
+
 // Four complex values (the electron components of one nuclear configuration):
 // 32 bytes in FP32, moved with one 256-bit access per thread (sm_100+), so a
 // warp reads or writes 1 KB contiguous per instruction; 64 bytes in FP64, two
@@ -151,6 +174,65 @@ __device__ __forceinline__ void apply_e2x2(Cx<T> (&y)[4], const Cx<T> (&q)[4], i
   }
 }
 
+// FP32 anisotropic spin-1/2 partner product on packed pairs: y += W q on the
+// electron of radical rr, W = U_p (digit 0) or U_p^dagger (digit 1), with
+// w[i] = (Re W_i, Re W_i, Im W_i, Im W_i) for entry i = 2 r + c.  The
+// products with Re W accumulate in A and those with Im W in B, both on
+// (re, im) pairs by fma.rn.f32x2 (two FMAs per instruction, no operand swap);
+// y = A + i B is formed once per configuration by pack_combine.
+template <int RR>
+__device__ __forceinline__ void e2x2_packed_rr(float2 (&A)[4], float2 (&B)[4],
+                                               const Cx<float> (&q)[4], const float4 (&w)[4]) {
+  float2 qv[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) qv[e] = make_float2(q[e].re, q[e].im);
+#pragma unroll
+  for (int s = 0; s < 2; ++s) {
+    // RR = 0: outputs/inputs s and 2 + s; RR = 1: 2 s and 2 s + 1
+    const int lo = RR == 0 ? s : 2 * s, hi = RR == 0 ? 2 + s : 2 * s + 1;
+    A[lo] = __ffma2_rn(make_float2(w[0].x, w[0].y), qv[lo], A[lo]);
+    B[lo] = __ffma2_rn(make_float2(w[0].z, w[0].w), qv[lo], B[lo]);
+    A[lo] = __ffma2_rn(make_float2(w[1].x, w[1].y), qv[hi], A[lo]);
+    B[lo] = __ffma2_rn(make_float2(w[1].z, w[1].w), qv[hi], B[lo]);
+    A[hi] = __ffma2_rn(make_float2(w[2].x, w[2].y), qv[lo], A[hi]);
+    B[hi] = __ffma2_rn(make_float2(w[2].z, w[2].w), qv[lo], B[hi]);
+    A[hi] = __ffma2_rn(make_float2(w[3].x, w[3].y), qv[hi], A[hi]);
+    B[hi] = __ffma2_rn(make_float2(w[3].z, w[3].w), qv[hi], B[hi]);
+  }
+}
+
+// rr is the same for every thread (one nucleus): a uniform branch, and the
+// register arrays keep compile-time indices.
+__device__ __forceinline__ void e2x2_packed(float2 (&A)[4], float2 (&B)[4],
+                                            const Cx<float> (&q)[4], int rr, const float4 (&w)[4]) {
+  if (rr == 0) e2x2_packed_rr<0>(A, B, q, w);
+  else e2x2_packed_rr<1>(A, B, q, w);
+}
+
+// y += A + i B (the packed partner sums of e2x2_packed).
+__device__ __forceinline__ void pack_combine(Cx<float> (&y)[4], const float2 (&A)[4],
+                                             const float2 (&B)[4]) {
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    y[e].re += A[e].x - B[e].y;
+    y[e].im += A[e].y + B[e].x;
+  }
+}
+
+// Fills the block's table of packed U_p / U_p^dagger entries of the spin-1/2
+// nuclei p < n (n * 8 threads from thread 0; barrier by the caller):
+// wt[(2 p + j) 4 + i] = (Re, Re, Im, Im) of entry i of U_p (j = 0) or of
+// U_p^dagger (j = 1; entry (r, c) = conj U_p(c, r)).
+__device__ __forceinline__ void fill_wtab_packed(float4* wt, const HamDev<float>& H, int n) {
+  const int t = (int)threadIdx.x;
+  if (t < n * 8) {
+    const int p = t >> 3, jj = (t >> 2) & 1, i = t & 3;
+    const int src = jj ? ((i & 1) << 1 | (i >> 1)) : i;
+    const float re = H.U[p][2 * src], im = jj ? -H.U[p][2 * src + 1] : H.U[p][2 * src + 1];
+    wt[(p * 2 + jj) * 4 + i] = make_float4(re, re, im, im);
+  }
+}
+
 // Partner contribution of nucleus p from configuration m + step * stride:
 // step = +1 uses c U_p (I_+ brings M-1 to M), step = -1 uses c U_p^dagger.
 template <typename T, bool ANISO>
@@ -272,7 +354,7 @@ __device__ __forceinline__ void half_nucleus(Cx<T> (&y)[4], T (&b1)[3], T (&b2)[
 // adds the electron block omega (S1z + S2z) + 2J S1.S2 - i kappa (2 P_S - 1) and
 // the diagonal-in-m hyperfine part (S1 . b1) x 1 + 1 x (S2 . b2),
 // b_i = sum_k M_k A_k e_z, then applies the Chebyshev scaling of field F.
-template <typename T, bool ANISO>
+template <typename T, bool ANISO, bool PACKED = false>
 __device__ __forceinline__ void finish_z(const HamDev<T>& H, const FieldDev<T>& F,
                                          const Cx<T> (&a)[4], Cx<T> (&y)[4], const T (&b1)[3],
                                          const T (&b2)[3], Cx<T> (&z)[4]) {
@@ -303,6 +385,14 @@ __device__ __forceinline__ void finish_z(const HamDev<T>& H, const FieldDev<T>& 
       cmac(y[2 * e1 + 1], h * b2[0], h * b2[1], lo);
       cmac(y[2 * e1 + 1], -h * b2[2], T(0), hi);
     }
+  } else if constexpr (PACKED) {
+    const float sp = 0.5f * (b1[2] + b2[2]), sm = 0.5f * (b1[2] - b2[2]);
+    cmac_packed(y[0], w + hJ + sp, kp, a[0]);
+    cmac_packed(y[1], -hJ + sm, 0.f, a[1]);
+    cmac_packed(y[1], Je, kp, a[2]);
+    cmac_packed(y[2], Je, kp, a[1]);
+    cmac_packed(y[2], -hJ - sm, 0.f, a[2]);
+    cmac_packed(y[3], -w + hJ - sp, kp, a[3]);
   } else {
     const T sp = T(0.5) * (b1[2] + b2[2]), sm = T(0.5) * (b1[2] - b2[2]);
     cmac(y[0], w + hJ + sp, kp, a[0]);
@@ -466,6 +556,20 @@ __device__ __forceinline__ void step_body(const HamDev<T>& H, const SysTab<T>& S
     for (int e = 0; e < 4; ++e) a[e] = {T(0), T(0)};
   }
   tile_put(tile, blockDim.x, threadIdx.x, a);
+  // anisotropic FP64: W[p][j] = U_p (j = 0) and U_p^dagger (j = 1) of the
+  // inner nuclei, entry (r, c) at 2 r + c, (re, im); FP32: the packed table
+  // of every spin-1/2 nucleus (fill_wtab_packed)
+  constexpr bool kPacked = ANISO && sizeof(T) == 4;
+  __shared__ Cx<T> wtab[ANISO && !kPacked ? kInnerBits * 2 * 4 : 1];
+  __shared__ float4 wtp[kPacked ? kMaxNucDev * 2 * 4 : 1];
+  if (kPacked) {
+    fill_wtab_packed(wtp, reinterpret_cast<const HamDev<float>&>(H), H.n_half);
+  } else if (ANISO && (int)threadIdx.x < n_in * 8) {
+    const int p = threadIdx.x >> 3, jj = (threadIdx.x >> 2) & 1, i = threadIdx.x & 3;
+    const int src = jj ? ((i & 1) << 1 | (i >> 1)) : i;  // U^dagger(r, c) = conj U(c, r)
+    const T re = H.U[p][2 * src], im = H.U[p][2 * src + 1];
+    wtab[(p * 2 + jj) * 4 + i] = {re, jj ? -im : im};
+  }
   __syncthreads();
   if (!valid) {  // no barrier below
     // the tensor-core integral reads whole 16-configuration chunks: keep the
@@ -483,6 +587,26 @@ __device__ __forceinline__ void step_body(const HamDev<T>& H, const SysTab<T>& S
   for (int e = 0; e < 4; ++e) y[e] = {T(0), T(0)};
   T b1[3] = {T(0), T(0), T(0)}, b2[3] = {T(0), T(0), T(0)};
 
+  if constexpr (kPacked) {
+    // FP32 anisotropic: every spin-1/2 nucleus on packed pairs
+    float2 A[4], B[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) A[e] = B[e] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int p = 0; p < kMaxNucDev; ++p) {
+      if (p < H.n_half) {
+        const unsigned j = (m >> p) & 1u;
+        Cx<float> q[4];
+        if (p < kInnerBits) tile_get(tile, blockDim.x, threadIdx.x ^ (1u << p), q);
+        else load4(c + (size_t)(m ^ (1u << p)) * 8, q);
+        const float4* wp = wtp + (p * 2 + j) * 4;
+        const float4 w[4] = {wp[0], wp[1], wp[2], wp[3]};
+        add_field(b1, b2, H.rad[p], j ? T(-0.5) : T(0.5), H.v[p]);
+        e2x2_packed(A, B, q, H.rad[p], w);
+      }
+    }
+    pack_combine(reinterpret_cast<Cx<float>(&)[4]>(y), A, B);
+  } else {
   // spin-1/2 nuclei inside the block: partner from shared memory
 #pragma unroll
   for (int p = 0; p < kInnerBits; ++p) {
@@ -490,19 +614,45 @@ __device__ __forceinline__ void step_body(const HamDev<T>& H, const SysTab<T>& S
       const unsigned j = (m >> p) & 1u;
       Cx<T> q[4];
       tile_get(tile, blockDim.x, threadIdx.x ^ (1u << p), q);
-      half_nucleus<T, ANISO>(y, b1, b2, H, p, j, q);
+      if (ANISO) {
+        // U_p (j = 0) or U_p^dagger (j = 1) from the block's table: two
+        // vector loads instead of a select per matrix entry
+        T mr[4], mi[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          mr[i] = wtab[(p * 2 + j) * 4 + i].re;
+          mi[i] = wtab[(p * 2 + j) * 4 + i].im;
+        }
+        add_field(b1, b2, H.rad[p], j ? T(-0.5) : T(0.5), H.v[p]);
+        apply_e2x2(y, q, H.rad[p], mr, mi);
+      } else {
+        half_nucleus<T, ANISO>(y, b1, b2, H, p, j, q);
+      }
     }
   }
-  // spin-1/2 nuclei outside the block (only when blockDim = 256): global partner
+  // spin-1/2 nuclei outside the block (only when blockDim = 256): global
+  // partner; the digit (m >> p) & 1 = (blockIdx.x >> (p - 8)) & 1 is the same
+  // for the whole block, so the anisotropic form branches on it uniformly and
+  // takes U_p or U_p^dagger straight from the constants
 #pragma unroll
   for (int p = kInnerBits; p < kMaxNucDev; ++p) {
     if (p < H.n_half) {
-      const unsigned j = (m >> p) & 1u;
       const unsigned mp = m ^ (1u << p);
       Cx<T> q[4];
       load4(c + (size_t)mp * 8, q);
-      half_nucleus<T, ANISO>(y, b1, b2, H, p, j, q);
+      if (ANISO) {
+        if ((blockIdx.x >> (p - kInnerBits)) & 1u) {
+          add_field(b1, b2, H.rad[p], T(-0.5), H.v[p]);
+          add_partner_q<T, true>(y, q, H.rad[p], H.U[p], T(1), false);
+        } else {
+          add_field(b1, b2, H.rad[p], T(0.5), H.v[p]);
+          add_partner_q<T, true>(y, q, H.rad[p], H.U[p], T(1), true);
+        }
+      } else {
+        half_nucleus<T, ANISO>(y, b1, b2, H, p, (m >> p) & 1u, q);
+      }
     }
+  }
   }
   // spin-1 nuclei: base-3 digits; partners +1 (j < 2) and -1 (j > 0), both sqrt 2
   unsigned qd = m >> H.n_half;
@@ -662,6 +812,8 @@ __global__ void __launch_bounds__(kBulkTile, 2) k_cheb_step_bulk(
     load4(prev + off, pv);
     load4_rw(acc + off, sa);
   }
+  __shared__ float4 wtp[ANISO ? kMaxNucDev * 2 * 4 : 1];
+  if (ANISO) fill_wtab_packed(wtp, H, H.n_half);
   __syncthreads();  // the barriers are initialised before anyone polls them
   if (!bulk_wait(bar_own) ) {
     if (S.err) atomicOr(S.err, 1);
@@ -675,12 +827,25 @@ __global__ void __launch_bounds__(kBulkTile, 2) k_cheb_step_bulk(
 #pragma unroll
   for (int e = 0; e < 4; ++e) y[e] = {0.f, 0.f};
   float b1[3] = {0.f, 0.f, 0.f}, b2[3] = {0.f, 0.f, 0.f};
+  // anisotropic: the spin-1/2 products on packed pairs, in the same order as
+  // k_cheb_step (results identical)
+  float2 A[4], B[4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) A[e] = B[e] = make_float2(0.f, 0.f);
   // spin-1/2 nuclei inside the tile
 #pragma unroll
   for (int p = 0; p < kInnerBits; ++p) {
     Cx<float> q[4];
     tile_get_aos(tiles, t ^ (1u << p), q);
-    half_nucleus<float, ANISO>(y, b1, b2, H, p, (m >> p) & 1u, q);
+    const unsigned j = (m >> p) & 1u;
+    if (ANISO) {
+      const float4* wp = wtp + (p * 2 + j) * 4;
+      const float4 w[4] = {wp[0], wp[1], wp[2], wp[3]};
+      add_field(b1, b2, H.rad[p], j ? -0.5f : 0.5f, H.v[p]);
+      e2x2_packed(A, B, q, H.rad[p], w);
+    } else {
+      half_nucleus<float, ANISO>(y, b1, b2, H, p, j, q);
+    }
   }
   if (!bulk_wait(bar_part)) {
     if (S.err) atomicOr(S.err, 1);
@@ -693,9 +858,18 @@ __global__ void __launch_bounds__(kBulkTile, 2) k_cheb_step_bulk(
     if (p < H.n_half) {
       Cx<float> q[4];
       tile_get_aos(tiles + (size_t)(1 + p - kInnerBits) * kBulkTile * 8, t, q);
-      half_nucleus<float, ANISO>(y, b1, b2, H, p, (c0 >> p) & 1u, q);
+      const unsigned j = (c0 >> p) & 1u;
+      if (ANISO) {
+        const float4* wp = wtp + (p * 2 + j) * 4;
+        const float4 w[4] = {wp[0], wp[1], wp[2], wp[3]};
+        add_field(b1, b2, H.rad[p], j ? -0.5f : 0.5f, H.v[p]);
+        e2x2_packed(A, B, q, H.rad[p], w);
+      } else {
+        half_nucleus<float, ANISO>(y, b1, b2, H, p, j, q);
+      }
     }
   }
+  if (ANISO) pack_combine(y, A, B);
   // nuclei of higher spin: partners j + 1 (through U) and j - 1 (through U^dagger)
   int slot = 1 + H.n_half - kInnerBits;
   unsigned qd = c0 >> H.n_half;
@@ -1197,7 +1371,7 @@ __global__ void __launch_bounds__(ClusterCfg<KPT>::kNT, 1) k_macro_cluster(
       }
       const float b1[3] = {0.f, 0.f, bz1}, b2[3] = {0.f, 0.f, bz2};
       Cx<float> z[4];
-      finish_z<float, false>(H, F, a, y, b1, b2, z);
+      finish_z<float, false, true>(H, F, a, y, b1, b2, z);
       Cx<float> ph[4], s[4];
       float2* al = accs + l;  // accumulator of l >= NT, plane e at + e apl
       if (n == 1) {
@@ -1206,8 +1380,8 @@ __global__ void __launch_bounds__(ClusterCfg<KPT>::kNT, 1) k_macro_cluster(
         for (int e = 0; e < 4; ++e) {
           ph[e] = z[e];
           s[e] = {0.f, 0.f};
-          cmac(s[e], cl[0], cl[1], a[e]);
-          cmac(s[e], c0r, c0i, a[e]);
+          cmac_packed(s[e], cl[0], cl[1], a[e]);
+          cmac_packed(s[e], c0r, c0i, a[e]);
         }
         float* x0 = Xr + xj[j];
         const float rs = 0.70710678118654752440f;
@@ -1230,8 +1404,8 @@ __global__ void __launch_bounds__(ClusterCfg<KPT>::kNT, 1) k_macro_cluster(
       }
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
-        cmac(s[e], clr, cli, ph[e]);
-        cmac(s[e], cr, ci, ph[e]);
+        cmac_packed(s[e], clr, cli, ph[e]);
+        cmac_packed(s[e], cr, ci, ph[e]);
       }
       if (j == 0) {
 #pragma unroll

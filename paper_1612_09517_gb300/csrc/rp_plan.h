@@ -88,9 +88,14 @@ long long basis_draw(uint64_t seed, uint32_t pair, long long sample, long long Z
 // propagations (the size of the largest class).
 long long sector_table(const HostSystem& hs, std::vector<int>* rank, std::vector<int>* n_of);
 
-// Kernel path rp_yields takes for kernel = 0 on this system in FP32 (2: whole
-// macro-step in one CTA, 4: on a thread-block cluster, 1: per-term kernels),
-// and in *cluster_ok whether kernel = 4 applies to it (rp_api.cu).
+// Kernel path rp_yields takes for kernel = 0 on this system in FP32 (5: one
+// persistent launch, 2: whole macro-step in one CTA, 4: on a thread-block
+// cluster, 1: per-term kernels), and in *cluster_ok whether kernel = 4
+// applies to it (rp_api.cu).
 int default_kernel_fp32(const HostSystem& hs, bool* cluster_ok);
+
+// Whether kernel = 0 takes the persistent launch for a slot of Zslot
+// configurations (<= the one-CTA limit) holding n_systems systems.
+bool persistent_default(long long Zslot, int n_systems);
 
 }  // namespace rp

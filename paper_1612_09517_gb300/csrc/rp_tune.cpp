@@ -153,8 +153,10 @@ rp_status rp_tune(rp_system* s, double B, int rows, const rp_options* base, rp_o
   // kernel 4 only where a row fits a thread-block cluster (FP32, isotropic)
   const bool staged = o.precision == RP_FP32 && s->hs.n_half >= 8;
   bool cluster_ok = false;
-  const int default_kernel = o.precision == RP_FP32 ? rp::default_kernel_fp32(s->hs, &cluster_ok)
-                                                    : (Z <= small_max ? 2 : 1);
+  int default_kernel = o.precision == RP_FP32
+                           ? rp::default_kernel_fp32(s->hs, &cluster_ok)
+                           : (Z <= small_max ? (rp::persistent_default(Z, 1) ? 5 : 2) : 1);
+  if (default_kernel == 5 && o.graph) default_kernel = 2;  // kernel 0 with graph replay
   for (int nc : ncs)
     for (int g = 0; g <= 1; ++g) {
       cands.push_back({1, nc, g});

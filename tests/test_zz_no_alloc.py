@@ -37,6 +37,19 @@ def _close(a, b, prec):
     return float(np.max(np.abs(a - b) / scale)) < TOL[prec]
 
 
+def _close_out(a, b, prec):
+    """Per-field output rows (Phi_S, Phi_T, SE_S, SE_T, survival): the means
+    relative to themselves; the standard errors (Eq. 23) on the scale of the
+    yields they are computed from, since |d SE| <= 2 max_i |d phi_i| / sqrt(M)
+    and an SE far below the yields (the basis-state trace) has no relative
+    accuracy of its own in FP32."""
+    means = [0, 1, 4]
+    if not _close(a[:, means], b[:, means], prec):
+        return False
+    scale = np.maximum(np.max(np.abs(b[:, :2]), axis=1, keepdims=True), 1e-3)
+    return float(np.max(np.abs(a[:, 2:4] - b[:, 2:4]) / scale)) < TOL[prec]
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_static_scratch_matches_allocating_entry_point(prec):
     from paper_1612_09517_gb300 import rp
@@ -51,7 +64,7 @@ def test_static_scratch_matches_allocating_entry_point(prec):
         a = rp.rp_yields_static(sy.handle, fields, M, 4, T, o, per_sample=True)
         b = rp.rp_yields(sy.handle, fields, M, 4, T, o, per_sample=True)
         assert _close(a["per_sample"], b["per_sample"], prec)
-        assert _close(a["out"], b["out"], prec)
+        assert _close_out(a["out"], b["out"], prec)
         assert a["stats"]["kernel_launches"] > 0 and a["stats"]["rows"] >= 1
 
 
@@ -70,7 +83,7 @@ def test_static_scratch_deterministic_trace_matches(prec):
         b = rp.rp_yields(sy.handle, fields, 2, 0, 2.0, o, per_sample=True, Z=sy.Z)
         assert a["per_sample"].shape == (3, sy.Z, 3)
         assert _close(a["per_sample"], b["per_sample"], prec)
-        assert _close(a["out"], b["out"], prec)
+        assert _close_out(a["out"], b["out"], prec)
         if max_rows:
             assert a["stats"]["rows"] == max_rows
 
