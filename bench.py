@@ -96,17 +96,17 @@ def _kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def _profile_traffic(kernel):
-    """DRAM bytes (read + write) per row of one launch of `kernel` from the
-    committed ncu figures (profiles/traffic.json), or None when absent or
+def _profile_traffic(kernel, key="dram_bytes_per_row"):
+    """A committed ncu figure of `kernel` (profiles/traffic.json): by default
+    the DRAM bytes (read + write) per row of one launch; None when absent or
     captured on a different kernel source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     d = json.load(open(p)).get(kernel)
-    if not d or d.get("kernel_source_sha256_16") != _kernel_source_hash():
+    if not d or d.get("kernel_source_sha256_16") != _kernel_source_hash() or key not in d:
         return None
-    return float(d["dram_bytes_per_row"])
+    return float(d[key])
 
 
 class ClockSampler:
@@ -251,6 +251,13 @@ def parse():
                     help="config 5: the 128-field curve to SE <= 1e-3 with the learned control "
                          "variate, then an independent plain M = 2000 estimate at four fields "
                          "to check its bias; prints one JSON line")
+    ap.add_argument("--config4", action="store_true",
+                    help="config 4 (256 radical pairs of uneven size) through rp_yields_batch on "
+                         "a stated subset: every pair at --c4-fields fields of its sweep x "
+                         "--c4-samples samples; time, work and the projection to the full "
+                         "workload by the plan's exact work; one JSON line")
+    ap.add_argument("--c4-fields", type=int, default=2)
+    ap.add_argument("--c4-samples", type=int, default=4)
     ap.add_argument("--table1", action="store_true",
                     help="the paper's model problem (Table I couplings, Z = 2^20): Phi_S(B) at 21 "
                          "fields 0-10 mT with M = 400 (and the first 100 and 200 samples, as in "
@@ -280,6 +287,10 @@ def parse():
     ap.add_argument("--ncu-case3", action="store_true",
                     help="profiling case of the anisotropic config-3 system (Z = 2359296): "
                          "2 rows, two macro-steps, ~4 GB on the device")
+    ap.add_argument("--ncu-case5", action="store_true",
+                    help="profiling case of the persistent launch (kernel 5): the first 8 "
+                         "config-4 pairs with Z <= 2048, 4 fields x 8 samples each, one "
+                         "rp_yields_batch call")
     ap.add_argument("--ncu-case", action="store_true",
                     help="run one small profiling case (192 rows, two macro-steps) and exit")
     return ap.parse_args()
@@ -542,6 +553,45 @@ def main():
                           "test_samples_per_field": n_test, "propagation_s": t_prop,
                           "results": res}), flush=True)
         return
+    if args.config4:
+        w4 = wl.config4()
+        systems = [rp.System(x.system) for x in w4]
+        nf = args.c4_fields
+        # evenly spaced fields of each pair's 32-field sweep, both ends included
+        fsel = np.unique(np.round(np.linspace(0, len(w4[0].fields) - 1, nf)).astype(int))
+        fields = [x.fields[fsel] for x in w4]
+        Ms = [args.c4_samples] * len(w4)
+        T4 = [x.t_max for x in w4]
+
+        def cfg_terms(sy_, x, flds, m):
+            # configuration-terms (Z x Chebyshev terms) of m samples at each field
+            return sum(sy_.plan(B, x.t_max, precision=prec)["n_macro"] * 88 * m * x.system.Z
+                       for B in flds)
+        sub = sum(cfg_terms(s_, x, f, m) for s_, x, f, m in zip(systems, w4, fields, Ms))
+        full = sum(cfg_terms(s_, x, x.fields, x.M) for s_, x in zip(systems, w4))
+        o = rp.rp_default_options(precision=prec, profile=1,
+                                  stream=torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = rp.rp_yields_batch(systems, fields, Ms, T4, 4, o)
+        wall = time.perf_counter() - t0
+        st = r["stats"]
+        Zs = np.array([x.system.Z for x in w4])
+        print(json.dumps({
+            "mode": "config4", "pairs": len(w4), "Z_range": [int(Zs.min()), int(Zs.max())],
+            "fields_per_pair": int(len(fsel)), "samples": args.c4_samples,
+            "propagations": int(st["propagations"]), "row_terms": int(st["row_terms"]),
+            "config_terms": sub, "wall_s": wall, "device_s": st["device_ms"] * 1e-3,
+            "kernel_launches": int(st["kernel_launches"]),
+            "step_kernels_hbm_GBps": (st["step_bytes"] / (st["step_ms"] * 1e-3) / 1e9)
+            if st["step_ms"] else None,
+            "fraction_of_full_workload": sub / full,
+            "full_workload_projected_s": wall * full / sub,
+            "note": "projection by the exact configuration-terms of the plans (Z x Chebyshev "
+                    "terms summed over pairs, fields and samples); the subset covers every "
+                    "pair, so every size class and kernel path of the full workload"}),
+              flush=True)
+        return
     if args.table1:
         gam = 176.085963023
         s1 = wl.table1(gam)
@@ -608,6 +658,17 @@ def main():
                           "note": "full trace (Z propagations per field) projected from the "
                                   "sector trace by the exact ratio of propagations, Z / n3; "
                                   "every propagation costs the same Chebyshev terms"}), flush=True)
+        return
+    if args.ncu_case5:
+        w4 = [x for x in wl.config4() if x.system.Z <= 2048][:8]
+        o = rp.rp_default_options(precision=rp.RP_FP32, kernel=5,
+                                  stream=torch.cuda.current_stream().cuda_stream)
+        r = rp.rp_yields_batch([rp.System(x.system) for x in w4], [x.fields[::8] for x in w4],
+                               [8] * len(w4), [x.t_max for x in w4], 3, o)
+        torch.cuda.synchronize()
+        print(json.dumps({"mode": "ncu-case5", "Z": [int(x.system.Z) for x in w4],
+                          "row_terms": int(r["stats"]["row_terms"]),
+                          "device_ms": r["stats"]["device_ms"]}), flush=True)
         return
     if args.ncu_case3:
         w3 = wl.config3()
@@ -743,6 +804,21 @@ def main():
             "hbm_algorithmic_GBps": step_bytes / (step_ms * 1e-3) / 1e9 if step_ms > 0 else None,
             "hbm_peak": peak, "hbm_peak_source": peak_src,
         }
+        # the kernel is bound by instruction issue (ncu: issue slots ~60 % busy
+        # on the active SMs): warp instructions per second from the committed
+        # per-configuration-term count against 4 issue slots per SM and clock
+        instr = _profile_traffic("k_macro_cluster", "thread_instructions_per_config_term")
+        if instr and step_ms > 0:
+            cfg_terms = row_terms * (n_c - 1) / n_c * sy.Z
+            issue = instr / 32.0 * cfg_terms / (step_ms * 1e-3)
+            peak_issue = n_sm * 4 * mhz * 1e6
+            roofline["issue"] = {
+                "achieved": issue, "peak": peak_issue, "unit": "warp instructions/s",
+                "frac": issue / peak_issue,
+                "source": f"{instr:.1f} thread instructions per configuration and term (ncu, "
+                          f"profiles/traffic.json) x configuration-terms / step time; peak "
+                          f"{n_sm} SMs x 4 issue slots x {mhz:.0f} MHz; clusters of 8 CTAs "
+                          "occupy 120 of the 152 SMs"}
     else:
         achieved = step_bytes / (step_ms * 1e-3) / 1e9 if step_ms > 0 else None
         traffic_per_row = _profile_traffic("k_cheb_step")
