@@ -380,13 +380,23 @@ class YieldEngine {
     if (n == 0) return;
     if (n > 2000000000LL) throw CudaFail{RP_EINVAL, "too many propagations for one launch"};
     std::vector<rp::PItem> h((size_t)n);
+    std::vector<double> cost((size_t)n);
     for (long long i = 0; i < n; ++i) {
       const Item& it = items[(size_t)i];
       h[(size_t)i] = rp::PItem{it.field, it.sys, it.n_macro, 0, it.sample, it.out};
+      cost[(size_t)i] = (double)it.n_macro * (double)sys_[it.sys]->Z;
       row_terms += (long long)it.n_macro * n_c_;
       // HBM: the singlet slices out and back in per macro-step
       step_bytes_all += 2.0 * n_c_ * (double)sys_[it.sys]->Z * 2.0 * sizeof(T) * it.n_macro;
     }
+    // longest items first (the CTAs take them in this order), so the launch
+    // does not end on one long item started last
+    std::vector<size_t> ord((size_t)n);
+    for (size_t i = 0; i < ord.size(); ++i) ord[i] = i;
+    std::stable_sort(ord.begin(), ord.end(), [&](size_t x, size_t y) { return cost[x] > cost[y]; });
+    std::vector<rp::PItem> hs((size_t)n);
+    for (size_t i = 0; i < ord.size(); ++i) hs[i] = h[ord[i]];
+    h.swap(hs);
     rp::PItem* d_items = ar_.get<rp::PItem>((size_t)n);
     ck(cudaMemcpyAsync(d_items, h.data(), h.size() * sizeof(rp::PItem), cudaMemcpyHostToDevice, st_),
        "h2d items");
