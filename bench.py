@@ -842,7 +842,7 @@ def main():
         }
 
     # plain FP64 form on the same GPU: measured end to end on a reduced
-    # workload beside the spec form, and projected to the full curve
+    # workload beside the FP32 + control-variate form, and projected to the full curve
     fp64 = None
     if args.precision == "fp32" and extras:
         o64 = rp.rp_default_options(precision=rp.RP_FP64, stream=stream.cuda_stream)
