@@ -251,6 +251,10 @@ def parse():
                     help="config 5: the 128-field curve to SE <= 1e-3 with the learned control "
                          "variate, then an independent plain M = 2000 estimate at four fields "
                          "to check its bias; prints one JSON line")
+    ap.add_argument("--config5", action="store_true",
+                    help="config 5 (the config-2 system over 128 fields 0-50 mT): the converged "
+                         "curve plain (rp_yields_converged) and with the learned control "
+                         "variate (rp_yields_cv), both end to end; one JSON line")
     ap.add_argument("--config4", action="store_true",
                     help="config 4 (256 radical pairs of uneven size) through rp_yields_batch on "
                          "a stated subset: every pair at --c4-fields fields of its sweep x "
@@ -394,6 +398,32 @@ def main():
                           "M_used": r["M_used"].tolist(),
                           "sigma": [round(float(x), 5) for x in sig],
                           "PhiS": r["out"][:, 0].tolist()}), flush=True)
+        return
+    if args.config5:
+        w5 = wl.config5()
+        o = rp.rp_default_options(precision=prec, stream=torch.cuda.current_stream().cuda_stream)
+        sy.yields([0.0], 2, 0, 0.05)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rpl = rp.rp_yields_converged(sy.handle, w5.fields, SE_TARGET, M_MIN, 4000, 0, w5.t_max, o)
+        wall_plain = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        rcv = rp.rp_yields_cv(sy.handle, w5.fields, SE_TARGET, M_MIN, 4000, 0, w5.t_max, o,
+                              rp.rp_cv_default_plan())
+        wall_cv = time.perf_counter() - t0
+        print(json.dumps({
+            "mode": "config5", "workload": "config5: " + WORKLOAD.split(": ", 1)[1]
+            .replace("64 fields", "128 fields"),
+            "plain": {"wall_s": wall_plain, "samples": int(rpl["M_used"].sum()),
+                      "row_terms": int(rpl["stats"]["row_terms"]),
+                      "max_SE": float(rpl["out"][:, 2].max())},
+            "cv": {"wall_s": wall_cv, "samples_plain": int(rcv["M_plain"].sum()),
+                   "samples_cv": int(rcv["M_cv"].sum()),
+                   "fields_with_cv": int(rcv["out"][:, 7].sum()),
+                   "control_variate_s": rcv["stats"]["cv_ms"] * 1e-3,
+                   "max_SE": float(rcv["out"][:, 1].max())},
+            "max_abs_diff_PhiS": float(np.max(np.abs(rcv["out"][:, 0] - rpl["out"][:, 0])))}),
+              flush=True)
         return
     if args.cv_bias:
         w5 = wl.config5()
