@@ -1164,6 +1164,15 @@ __device__ __forceinline__ void cluster_barrier() {
   asm volatile("barrier.cluster.arrive.release;\n\tbarrier.cluster.wait.acquire;" ::: "memory");
 }
 
+// The two halves of cluster_barrier, for work that needs neither (between them
+// a thread may only touch memory no other CTA writes before the wait).
+__device__ __forceinline__ void cluster_arrive() {
+  asm volatile("barrier.cluster.arrive.release;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_wait() {
+  asm volatile("barrier.cluster.wait.acquire;" ::: "memory");
+}
+
 // Complex values in shared memory (float2 = re, im).  Plain loads and stores,
 // so the compiler keeps them ordered against the cluster barrier (its memory
 // clobber) and schedules them freely between barriers; a peer CTA's shared
@@ -1425,13 +1434,31 @@ __global__ void __launch_bounds__(ClusterCfg<KPT>::kNT, 1) k_macro_cluster(
       if (n < n_c - 1) {
 #pragma unroll
         for (int e = 0; e < 4; ++e) stc(oth + e * Zl + l, ph[e]);
+      } else {
+        float* xo = Xr + xj[j] + xn;
+        const float rs = 0.70710678118654752440f;
+        xo[0] = (ph[1].re - ph[2].re) * rs;
+        xo[ximag] = (ph[1].im - ph[2].im) * rs;
       }
-      float* xo = Xr + xj[j] + xn;
-      const float rs = 0.70710678118654752440f;
-      xo[0] = (ph[1].re - ph[2].re) * rs;
-      xo[ximag] = (ph[1].im - ph[2].im) * rs;
     }
-    cluster_barrier();
+    // The singlet slices of phi_n go to global memory between the arrive and
+    // the wait, read back from this thread's own shared-memory entries (peers
+    // only read them now): the release of the next term's arrive then finds
+    // these stores long done instead of waiting for them.
+    cluster_arrive();
+    if (n < n_c - 1) {
+      const float rs = 0.70710678118654752440f;
+#pragma unroll
+      for (int j = 0; j < KPT; ++j) {
+        const unsigned l = tid + j * NT;
+        if (l >= Zl) continue;
+        const Cx<float> p1 = ldc(oth + 1u * Zl + l), p2 = ldc(oth + 2u * Zl + l);
+        float* xo = Xr + xj[j] + xn;
+        xo[0] = (p1.re - p2.re) * rs;
+        xo[ximag] = (p1.im - p2.im) * rs;
+      }
+    }
+    cluster_wait();
   }
   // psi(t + h) = the accumulator (no peer reads after the last barrier)
 #pragma unroll
