@@ -220,12 +220,11 @@ __device__ __forceinline__ void pack_combine(Cx<float> (&y)[4], const float2 (&A
 }
 
 // Fills the block's table of packed U_p / U_p^dagger entries of the spin-1/2
-// nuclei p < n (n * 8 threads from thread 0; barrier by the caller):
-// wt[(2 p + j) 4 + i] = (Re, Re, Im, Im) of entry i of U_p (j = 0) or of
-// U_p^dagger (j = 1; entry (r, c) = conj U_p(c, r)).
+// nuclei p < n (8 n entries, the block's threads strided over them; barrier
+// by the caller): wt[(2 p + j) 4 + i] = (Re, Re, Im, Im) of entry i of U_p
+// (j = 0) or of U_p^dagger (j = 1; entry (r, c) = conj U_p(c, r)).
 __device__ __forceinline__ void fill_wtab_packed(float4* wt, const HamDev<float>& H, int n) {
-  const int t = (int)threadIdx.x;
-  if (t < n * 8) {
+  for (int t = (int)threadIdx.x; t < n * 8; t += (int)blockDim.x) {
     const int p = t >> 3, jj = (t >> 2) & 1, i = t & 3;
     const int src = jj ? ((i & 1) << 1 | (i >> 1)) : i;
     const float re = H.U[p][2 * src], im = jj ? -H.U[p][2 * src + 1] : H.U[p][2 * src + 1];
@@ -572,11 +571,14 @@ __device__ __forceinline__ void step_body(const HamDev<T>& H, const SysTab<T>& S
   __shared__ float4 wtp[kPacked ? kMaxNucDev * 2 * 4 : 1];
   if (kPacked) {
     fill_wtab_packed(wtp, reinterpret_cast<const HamDev<float>&>(H), nhalf);
-  } else if (ANISO && (int)threadIdx.x < n_in * 8) {
-    const int p = threadIdx.x >> 3, jj = (threadIdx.x >> 2) & 1, i = threadIdx.x & 3;
-    const int src = jj ? ((i & 1) << 1 | (i >> 1)) : i;  // U^dagger(r, c) = conj U(c, r)
-    const T re = H.U[p][2 * src], im = H.U[p][2 * src + 1];
-    wtab[(p * 2 + jj) * 4 + i] = {re, jj ? -im : im};
+  } else if (ANISO) {
+    // 8 n_in entries (40 with a 32-thread block and 5 inner nuclei): strided
+    for (int t = (int)threadIdx.x; t < n_in * 8; t += (int)blockDim.x) {
+      const int p = t >> 3, jj = (t >> 2) & 1, i = t & 3;
+      const int src = jj ? ((i & 1) << 1 | (i >> 1)) : i;  // U^dagger(r, c) = conj U(c, r)
+      const T re = H.U[p][2 * src], im = H.U[p][2 * src + 1];
+      wtab[(p * 2 + jj) * 4 + i] = {re, jj ? -im : im};
+    }
   }
   __syncthreads();
   if (!valid) {  // no barrier below

@@ -55,6 +55,10 @@ MIXED = [
     ("spin3half_J", lambda: wl.random_isotropic(1, 2, two_I=[3, 1, 2], k_S=0.2, k_T=5.0, J=-0.5, seed=41)),
     ("no_nuclei", lambda: wl.SpinSystem([], [], np.zeros((0, 3, 3)), 1.5, 0.7, 0.4)),
     ("ragged_z", lambda: wl.random_isotropic(3, 2, two_I=[2, 1, 2, 2, 1], k_S=1.0, k_T=2.0, seed=42)),
+    # five anisotropic spin-1/2 nuclei, Z = 32: a 32-thread block holds the
+    # per-block U / U-dagger table of 40 entries (strided fill)
+    ("aniso_5half", lambda: wl.random_anisotropic(3, 2, two_I=[1] * 5, k_S=1.2, k_T=0.4, J=0.2,
+                                                  seed=48)),
 ]
 
 
