@@ -358,10 +358,10 @@ def main():
     import numpy as np
     import torch
     world, rank, local = _dist()
+    torch.cuda.set_device(local)  # before the process group, so NCCL binds this GPU
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
-    torch.cuda.set_device(local)
     from paper_1612_09517_gb300 import rp
     from paper_1612_09517_gb300 import workloads as wl
     rp.use_torch_allocator()
