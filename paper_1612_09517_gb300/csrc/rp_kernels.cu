@@ -223,13 +223,19 @@ __device__ __forceinline__ void pack_combine(Cx<float> (&y)[4], const float2 (&A
 // nuclei p < n (8 n entries, the block's threads strided over them; barrier
 // by the caller): wt[(2 p + j) 4 + i] = (Re, Re, Im, Im) of entry i of U_p
 // (j = 0) or of U_p^dagger (j = 1; entry (r, c) = conj U_p(c, r)).
+__device__ __forceinline__ void fill_wtab_entry(float4* wt, const HamDev<float>& H, int t) {
+  const int p = t >> 3, jj = (t >> 2) & 1, i = t & 3;
+  const int src = jj ? ((i & 1) << 1 | (i >> 1)) : i;
+  const float re = H.U[p][2 * src], im = jj ? -H.U[p][2 * src + 1] : H.U[p][2 * src + 1];
+  wt[(p * 2 + jj) * 4 + i] = make_float4(re, re, im, im);
+}
+
 __device__ __forceinline__ void fill_wtab_packed(float4* wt, const HamDev<float>& H, int n) {
-  for (int t = (int)threadIdx.x; t < n * 8; t += (int)blockDim.x) {
-    const int p = t >> 3, jj = (t >> 2) & 1, i = t & 3;
-    const int src = jj ? ((i & 1) << 1 | (i >> 1)) : i;
-    const float re = H.U[p][2 * src], im = jj ? -H.U[p][2 * src + 1] : H.U[p][2 * src + 1];
-    wt[(p * 2 + jj) * 4 + i] = make_float4(re, re, im, im);
-  }
+  // at most two entries per thread: 8 n <= 2 blockDim for every block size
+  // the launchers use (n <= log2 of the block for blocks below 256)
+  const int t = (int)threadIdx.x;
+  if (t < n * 8) fill_wtab_entry(wt, H, t);
+  if (t + (int)blockDim.x < n * 8) fill_wtab_entry(wt, H, t + (int)blockDim.x);
 }
 
 // Partner contribution of nucleus p from configuration m + step * stride:
